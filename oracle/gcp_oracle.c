@@ -299,16 +299,18 @@ double orc_model(int d, const int64_t *dims, int R, const double *A, const int32
  * contribution G_n(i_n, :) += w f'(x, m) prod_{k != n} A_k(i_k, :) for every
  * mode n (Eq. gcp-gradient, one nonzero of the gradient tensor).  With
  * semi != 0 the derivative is f'(x,m) - f'(0,m), the semi-stratified
- * nonzero value of Sec. 3.1.1. */
+ * nonzero value of Sec. 3.1.1, and the loss term f(x,m) - f(0,m) (the
+ * zero candidates already counted f(0,m) for every cell). */
 static double add_sample(int d, const int64_t *dims, const int64_t *off, int R, const double *A,
                          int loss, const int32_t *i, double x, double w, int semi, double *G)
 {
     double m = orc_model(d, dims, R, A, i);
     double f, df;
     orc_loss(loss, x, m, &f, &df);
-    if (semi) {
+    if (semi) { /* the same correction keeps the loss estimate unbiased too */
         double f0, df0;
         orc_loss(loss, 0.0, m, &f0, &df0);
+        f -= f0;
         df -= df0;
     }
     if (G) {

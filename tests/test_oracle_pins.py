@@ -229,17 +229,21 @@ def test_semi_stratified_gradient_is_unbiased_by_enumeration(loss):
     dims = [4, 3, 2]
     coords, vals, factors = _tiny(dims, 7, 61, loss)
     X = oracle.densify(dims, coords, vals)
-    _, Gfull = oracle.full_loss_grad(dims, factors, loss, X)
+    Ffull, Gfull = oracle.full_loss_grad(dims, factors, loss, X)
     N, M = len(vals), int(np.prod(dims))
     EG = [np.zeros_like(g) for g in Gfull]
+    EF = 0.0
     for e in range(N):
-        _, G = oracle.sampled_loss_grad(dims, factors, loss, coords[e:e + 1], [vals[e]], [N], semi=[1])
+        F, G = oracle.sampled_loss_grad(dims, factors, loss, coords[e:e + 1], [vals[e]], [N], semi=[1])
+        EF += F / N
         for n in range(3):
             EG[n] += G[n] / N
     for z in np.ndindex(*dims):
-        _, G = oracle.sampled_loss_grad(dims, factors, loss, np.array([z]), [0.0], [M], semi=[0])
+        F, G = oracle.sampled_loss_grad(dims, factors, loss, np.array([z]), [0.0], [M], semi=[0])
+        EF += F / M
         for n in range(3):
             EG[n] += G[n] / M
+    assert EF == pytest.approx(Ffull, rel=1e-12)
     for n in range(3):
         np.testing.assert_allclose(EG[n], Gfull[n], rtol=1e-11, atol=1e-12)
 
