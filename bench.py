@@ -1,0 +1,349 @@
+"""Benchmark of the stochastic GCP gradient step on GB300.
+
+Workload: a 4-way sparse count tensor 2000 x 1500 x 1000 x 200 with 5e7
+distinct nonzeros whose coordinates follow per-mode Zipf(1.1) marginals,
+values 1 + Poisson(3), Poisson loss, rank 32, FP32 factors, 2^20 nonzero +
+2^20 zero samples per gradient.  One step = one fused sampled gradient
+(sampling, model, loss, all-mode MTTKRP) plus one Adam update, through the
+C ABI.  The metric is gradient samples per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica (the path
+does not shard); value = all ranks' samples / the slowest rank's time.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GCP gradient samples/s & % HBM peak; BF16/batched vs plain FP32 at rel-err≤5e-3"
+WORKLOAD = ("zipf-count 4-way 2000x1500x1000x200, 5e7 nnz Zipf(1.1) coords, 1+Poisson(3) values, "
+            "Poisson loss, rank 32, p=q=2^20 stratified samples")
+KERNEL_SOURCES = ["paper_2605_20353_gb300/csrc/gcp_kernels.cu", "paper_2605_20353_gb300/csrc/gcp_device.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_grad_zipf_count_traffic.json")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def workload():
+    import synth
+
+    return synth.cached("zipf_count_full", lambda: synth.workload_zipf_count(scale=1.0))
+
+
+def algorithmic_bytes_per_sample(d, R, nnz, M, elt_bytes):
+    """Bytes one sample must move by the definition of the step: a nonzero
+    reads its d coordinates and value (4(d+1) B); a zero reads one 32-byte
+    hash bucket per rejection attempt (expected 1/(1-N/M)); both gather d
+    factor rows (elt_bytes R each) and add d gradient rows (4R each)."""
+    attempts = 1.0 / (1.0 - nnz / M)
+    rows = d * R * (elt_bytes + 4)
+    return 0.5 * (4 * (d + 1) + rows) + 0.5 * (32 * attempts + rows)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        if t.get("kernel_sha") == kernel_source_hash():
+            return t["dram_bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(w, skeys, n_samples, seed=3002, t=5):
+    """Oracle samples/s on n_samples of the workload (half nonzero, half zero)."""
+    import oracle
+
+    p = n_samples // 2
+    q = n_samples - p
+    t0 = time.perf_counter()
+    idx, x, wt, _ = oracle.stratified_samples(seed, t, p, q, w["dims"], w["coords"], w["vals"], skeys=skeys)
+    oracle.sampled_loss_grad(w["dims"], w["factors"], w["loss"], idx, x, wt)
+    return n_samples / (time.perf_counter() - t0)
+
+
+def cpu_baseline(w, target_s=10.0):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample."""
+    import numpy as np
+
+    import oracle
+
+    skeys = oracle.sorted_keys(w["dims"], w["coords"])
+    probe = cpu_oracle_rate(w, skeys, 1 << 14)
+    n = int(min(w["p"] + w["q"], max(1 << 14, probe * target_s)))
+    rate = cpu_oracle_rate(w, skeys, n)
+    return {"value": rate, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} samples ({n // 2} nonzero + {n - n // 2} zero) of the same workload, "
+                      f"sampling + FP64 loss + all-mode gradient, one thread"}
+
+
+def run_reference(args):
+    """The oracle arm: each step = the oracle on a bounded sample of the
+    workload, sized so the whole run stays within a few minutes."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    w = workload()
+    skeys = oracle.sorted_keys(w["dims"], w["coords"])
+    probe = cpu_oracle_rate(w, skeys, 1 << 12)
+    per_step = max(64, int(probe * 90.0 / max(1, args.steps + args.warmup)))
+    per_step = min(per_step, w["p"] + w["q"])
+    for i in range(args.warmup):
+        cpu_oracle_rate(w, skeys, per_step, t=100 + i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        cpu_oracle_rate(w, skeys, per_step, t=i)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "samples_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} samples per step of the same workload"},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2605_20353_gb300 as gcp
+    from paper_2605_20353_gb300 import build
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    gcp.load()
+    if rank == 0:
+        w = workload()
+    if dist:
+        dist.barrier()
+    if rank != 0:
+        w = workload()
+    dims, R, p, q = w["dims"], w["rank"], w["p"], w["q"]
+    S = p + q
+    stream = torch.cuda.current_stream()
+
+    def make(dtype):
+        ctx = gcp.gcp_create(dims, w["coords"], w["vals"], R, "poisson", dtype=dtype, seed=3002 + rank,
+                             stream=stream)
+        ctx.set_factors(w["factors"])
+        return ctx
+
+    adam = gcp.AdamParams(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, lower=0.0)
+
+    def timed_loop(ctx, steps, warmup, profile):
+        for i in range(warmup):
+            ctx.grad_async(10_000 + i, p, q)
+            ctx.adam_step(adam, i + 1)
+        ctx.sync()
+        if profile:
+            ctx.profile(True)
+            ctx.profile_read()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            ctx.grad_async(i, p, q)
+            ctx.adam_step(adam, warmup + i + 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ctx.sync()
+        ms = e0.elapsed_time(e1)
+        kms, nl = ctx.profile_read() if profile else (0.0, 0)
+        ctx.profile(False)
+        return ms, kms, nl
+
+    ctx = make("fp32")
+    with ClockSampler(local) as clk:
+        ms, kernel_ms, launches = timed_loop(ctx, args.steps, args.warmup, profile=True)
+    clocks = clk.summary()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    ms_per_step = ms / args.steps
+    value = world * S * args.steps / (ms / 1e3)
+
+    # end to end through the public API with host buffers: factors in from
+    # pinned host memory, gradient and loss back to the host every step
+    n_e2e = max(3, min(args.steps, 200))
+    A_host = torch.from_numpy(np.concatenate([a.ravel() for a in w["factors"]])).pin_memory()
+    G_host = torch.empty(ctx.num_params, dtype=torch.float32).pin_memory()
+    for i in range(3):
+        ctx.set_factors(A_host.numpy())
+        ctx.grad(20_000 + i, p, q, G_out=G_host)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(n_e2e):
+        _check = gcp.load().gcp_set_factors(ctx.handle, A_host.data_ptr())
+        assert _check == 0
+        loss, _ = ctx.grad(i, p, q, G_out=G_host)
+        ctx.adam_step(adam, i + 1)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * S * n_e2e / float(e2e_t.item())
+    ctx.close()
+
+    # BF16 factor storage, same workload
+    ctx_bf = make("bf16")
+    ms_bf, kms_bf, nl_bf = timed_loop(ctx_bf, max(3, args.steps // 2), args.warmup, profile=True)
+    ctx_bf.close()
+    bf16_value = S * max(3, args.steps // 2) / (ms_bf / 1e3)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    bps = algorithmic_bytes_per_sample(4, R, len(w["vals"]), float(np.prod(dims, dtype=np.float64)), 4)
+    bps_bf = algorithmic_bytes_per_sample(4, R, len(w["vals"]), float(np.prod(dims, dtype=np.float64)), 2)
+    kernel_avg_s = kernel_ms / 1e3 / launches
+    achieved = bps * S / kernel_avg_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": measured_traffic(), "kernel": "k_fused<4,float>",
+                "bytes_per_sample": bps, "kernel_ms_per_launch": kernel_avg_s * 1e3,
+                "peak_source": f"{peak_kind} HBM copy bandwidth"}
+    base = cpu_baseline(w)
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "samples_per_step": S, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (1.6 GB records, 2.1 GB hash set); factors and gradient "
+                             "(0.6 MB each) stay L2-resident across steps as in training",
+                       "step": "fused sampled gradient + Adam"},
+            "roofline": roofline, "cpu_baseline": base,
+            "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(A_host.numel() * 4),
+                    "d2h_bytes_per_step": int(G_host.numel() * 4 + 8)},
+            "gpu_launches": 3 * args.steps, "clocks": clocks,
+            "variants": {"bf16_factors": {"value": bf16_value, "unit": "samples/s",
+                                          "kernel_ms_per_launch": kms_bf / max(1, nl_bf),
+                                          "achieved_gbs": bps_bf * S / (kms_bf / 1e3 / max(1, nl_bf)) / 1e9}}}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

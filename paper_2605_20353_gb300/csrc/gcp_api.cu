@@ -1,0 +1,627 @@
+// gcp_api.cu -- the C ABI of include/gcp.h: context set-up, argument checks,
+// the stratified weights of Sec. 3.1.1, kernel launches and the GCP-Adam
+// epoch loop (Algorithm 2 on one GPU).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gcp_internal.h"
+
+namespace {
+
+thread_local std::string g_create_err;
+
+struct DeviceGuard {  // make the context's device current for one call
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+gcp_status fail(gcp_ctx *c, gcp_status code, const std::string &msg) {
+    if (c)
+        c->err = msg;
+    else
+        g_create_err = msg;
+    return code;
+}
+
+gcp_status cuda_fail(gcp_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? GCP_ERR_OOM : GCP_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define GCP_CUDA(ctx, call)                                      \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+uint64_t next_pow2(uint64_t v) {
+    uint64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// status word -> first gcp_status code set
+gcp_status status_code(int bits) {
+    for (int c = 1; c < 31; ++c)
+        if (bits & (1 << c)) return (gcp_status)c;
+    return GCP_OK;
+}
+
+const char *status_text(gcp_status s) {
+    switch (s) {
+    case GCP_ERR_DUPLICATE: return "duplicate nonzero coordinates";
+    case GCP_ERR_HASH_FULL: return "nonzero hash set is full";
+    case GCP_ERR_SAMPLER_EXHAUSTED: return "a zero draw hit nonzeros max_attempts times (tensor too dense)";
+    case GCP_ERR_NONFINITE: return "non-finite loss";
+    default: return "device error";
+    }
+}
+
+// Read and clear the device status word; synchronises the stream.
+gcp_status collect(gcp_ctx *c) {
+    GCP_CUDA(c, cudaMemcpyAsync(c->h_status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    GCP_CUDA(c, cudaStreamSynchronize(c->st));
+    const int bits = *c->h_status;
+    if (bits) {
+        GCP_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->st));
+        const gcp_status s = status_code(bits);
+        return fail(c, s, status_text(s));
+    }
+    return GCP_OK;
+}
+
+void destroy_buffers(gcp_ctx *c) {
+    cudaFree(c->rec);
+    cudaFree(c->hkeys);
+    cudaFree(c->X);
+    cudaFree(c->A);
+    cudaFree(c->Abf);
+    cudaFree(c->G);
+    cudaFree(c->B);
+    cudaFree(c->C);
+    cudaFree(c->partials);
+    cudaFree(c->dloss);
+    cudaFree(c->status);
+    cudaFree(c->det_scratch);
+    cudaFree(c->bk_A);
+    cudaFree(c->bk_B);
+    cudaFree(c->bk_C);
+    cudaFreeHost(c->h_status);
+    cudaFreeHost(c->h_loss);
+    for (auto &ev : c->prof_ev) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    c->prof_ev.clear();
+}
+
+// Event pair for the next timed launch (reused across reads).
+gcp_status prof_begin(gcp_ctx *c, cudaEvent_t *stop) {
+    *stop = nullptr;
+    if (!c->prof) return GCP_OK;
+    if (c->prof_used == c->prof_ev.size()) {
+        std::pair<cudaEvent_t, cudaEvent_t> ev;
+        GCP_CUDA(c, cudaEventCreate(&ev.first));
+        GCP_CUDA(c, cudaEventCreate(&ev.second));
+        c->prof_ev.push_back(ev);
+    }
+    auto &ev = c->prof_ev[c->prof_used++];
+    GCP_CUDA(c, cudaEventRecord(ev.first, c->st));
+    *stop = ev.second;
+    return GCP_OK;
+}
+
+// Shape, options and model buffers common to sparse and dense contexts.
+gcp_status init_common(gcp_ctx *c, int32_t ndim, const int64_t *dims, int32_t rank, int32_t loss,
+                       const gcp_options *opt) {
+    if (ndim < 2 || ndim > GCP_MAX_NDIM) return fail(nullptr, GCP_ERR_ARG, "ndim must be in 2..8");
+    if (!dims) return fail(nullptr, GCP_ERR_ARG, "dims is NULL");
+    if (rank < 1 || rank > GCP_MAX_RANK) return fail(nullptr, GCP_ERR_ARG, "rank must be in 1..128");
+    if (loss < GCP_GAUSSIAN || loss > GCP_GAMMA) return fail(nullptr, GCP_ERR_ARG, "unknown loss");
+    gcp_options_default(&c->opt);
+    if (opt) c->opt = *opt;
+    if (c->opt.factor_dtype != GCP_FP32 && c->opt.factor_dtype != GCP_BF16)
+        return fail(nullptr, GCP_ERR_ARG, "unknown factor dtype");
+    if (c->opt.mttkrp != GCP_MTTKRP_ATOMIC && c->opt.mttkrp != GCP_MTTKRP_DETERMINISTIC)
+        return fail(nullptr, GCP_ERR_ARG, "unknown MTTKRP variant");
+    if (c->opt.max_attempts < 0) return fail(nullptr, GCP_ERR_ARG, "max_attempts < 0");
+    if (c->opt.max_attempts == 0) c->opt.max_attempts = 64;
+    if (c->opt.hash_max_load == 0.0) c->opt.hash_max_load = 0.3;
+    if (!(c->opt.hash_max_load > 0.0 && c->opt.hash_max_load <= 0.5))
+        return fail(nullptr, GCP_ERR_ARG, "hash_max_load must be in (0, 0.5]");
+    c->d = ndim;
+    c->R = rank;
+    c->loss = loss;
+    c->st = static_cast<cudaStream_t>(c->opt.stream);
+    cudaGetDevice(&c->device);
+    unsigned __int128 M = 1;
+    for (int k = 0; k < ndim; ++k) {
+        if (dims[k] < 1 || dims[k] > INT32_MAX) return fail(nullptr, GCP_ERR_ARG, "mode size out of range");
+        c->dims[k] = dims[k];
+        M *= (unsigned __int128)dims[k];
+        if (M >= ((unsigned __int128)1 << 63)) return fail(nullptr, GCP_ERR_ARG, "prod(dims) must be < 2^63");
+    }
+    c->M = (double)(uint64_t)M;
+    c->stride[ndim - 1] = 1;
+    for (int k = ndim - 2; k >= 0; --k) c->stride[k] = c->stride[k + 1] * (uint64_t)dims[k + 1];
+    c->total_rows = 0;
+    for (int k = 0; k < ndim; ++k) {
+        c->rowoff[k] = c->total_rows;
+        c->total_rows += dims[k];
+    }
+    const int vec = c->opt.factor_dtype == GCP_BF16 ? 8 : 4;
+    int L = 1, log2L = 0;
+    while (L * vec < rank) {
+        L <<= 1;
+        ++log2L;
+    }
+    c->Rp = L * vec;
+    c->log2L = log2L;
+
+    const size_t nparam = (size_t)c->total_rows * c->Rp;
+    cudaError_t e;
+    if ((e = cudaMalloc(&c->A, nparam * 4)) || (e = cudaMalloc(&c->G, nparam * 4)) ||
+        (e = cudaMalloc(&c->B, nparam * 4)) || (e = cudaMalloc(&c->C, nparam * 4)) ||
+        (e = cudaMalloc(&c->dloss, 4 * sizeof(double))) || (e = cudaMalloc(&c->status, sizeof(int))) ||
+        (e = cudaMallocHost(&c->h_status, sizeof(int))) || (e = cudaMallocHost(&c->h_loss, 4 * sizeof(double))))
+        return cuda_fail(nullptr, e, "allocating model buffers");
+    if (c->opt.factor_dtype == GCP_BF16 && (e = cudaMalloc(&c->Abf, nparam * 2)))
+        return cuda_fail(nullptr, e, "allocating BF16 factors");
+    c->max_blocks = gcpk::fused_max_blocks(ndim, c->opt.factor_dtype == GCP_BF16);
+    if ((e = cudaMalloc(&c->partials, (size_t)c->max_blocks * 4 * sizeof(double))))
+        return cuda_fail(nullptr, e, "allocating partials");
+    if ((e = cudaMemsetAsync(c->A, 0, nparam * 4, c->st)) || (e = cudaMemsetAsync(c->G, 0, nparam * 4, c->st)) ||
+        (e = cudaMemsetAsync(c->B, 0, nparam * 4, c->st)) || (e = cudaMemsetAsync(c->C, 0, nparam * 4, c->st)) ||
+        (e = cudaMemsetAsync(c->status, 0, sizeof(int), c->st)) ||
+        (c->Abf && (e = cudaMemsetAsync(c->Abf, 0, nparam * 2, c->st))))
+        return cuda_fail(nullptr, e, "clearing model buffers");
+    return GCP_OK;
+}
+
+gcpk::SampleSpec sample_spec(const gcp_ctx *c, uint64_t iter, int64_t p, int64_t q) {
+    gcpk::SampleSpec s{};
+    s.d = c->d;
+    for (int k = 0; k < c->d; ++k) {
+        s.dims[k] = c->dims[k];
+        s.stride[k] = c->stride[k];
+    }
+    s.nnz = c->nnz;
+    s.rec = c->rec;
+    s.rec_words = c->rec_words;
+    s.hkeys = c->hkeys;
+    s.hbmask = c->hbmask;
+    s.dense = c->X;
+    s.seed = c->opt.seed;
+    s.iter = iter;
+    s.p = p;
+    s.q = q;
+    s.sampling = c->opt.sampling;
+    s.max_attempts = c->opt.max_attempts;
+    s.status = c->status;
+    return s;
+}
+
+// Per-sample weights of Sec. 3.1.1: N/p for nonzeros, (M-N)/q for zeros;
+// semi-stratified zero candidates cover all M cells (M/q); dense uniform
+// sampling weighs each of the p cells M/p.
+void weights(const gcp_ctx *c, int64_t p, int64_t q, double &w_nz, double &w_z) {
+    if (c->opt.sampling == GCP_SAMPLING_UNIFORM) {
+        w_nz = p > 0 ? c->M / (double)p : 0.0;
+        w_z = 0.0;
+        return;
+    }
+    w_nz = p > 0 ? (double)c->nnz / (double)p : 0.0;
+    if (c->opt.sampling == GCP_SAMPLING_SEMI_STRATIFIED)
+        w_z = q > 0 ? c->M / (double)q : 0.0;
+    else
+        w_z = q > 0 ? (c->M - (double)c->nnz) / (double)q : 0.0;
+}
+
+gcp_status check_counts(gcp_ctx *c, int64_t p, int64_t q) {
+    if (p < 0 || q < 0) return fail(c, GCP_ERR_ARG, "negative sample count");
+    if (c->dense && q != 0) return fail(c, GCP_ERR_ARG, "dense tensors take p uniform samples and q = 0");
+    if (p + q > ((int64_t)1 << 40)) return fail(c, GCP_ERR_ARG, "too many samples");
+    return GCP_OK;
+}
+
+// One fused pass: loss always, gradient into c->G when `grad`.
+gcp_status run_fused(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad, const float *dscale) {
+    gcp_status s = check_counts(c, p, q);
+    if (s) return s;
+    double w_nz, w_z;
+    weights(c, p, q, w_nz, w_z);
+    gcpk::FusedSpec f{};
+    f.s = sample_spec(c, iter, p, q);
+    f.F = c->Abf ? c->Abf : (const void *)c->A;
+    f.G = grad ? c->G : nullptr;
+    f.Rp = c->Rp;
+    f.log2L = c->log2L;
+    for (int k = 0; k < c->d; ++k) f.rowoff[k] = c->rowoff[k];
+    f.loss = c->loss;
+    f.w_nz = (float)w_nz;
+    f.w_z = (float)w_z;
+    f.dscale = dscale;
+    f.partials = c->partials;
+    if (grad) GCP_CUDA(c, cudaMemsetAsync(c->G, 0, (size_t)c->total_rows * c->Rp * 4, c->st));
+    int blocks = 0;
+    cudaEvent_t stop = nullptr;
+    if ((s = prof_begin(c, &stop))) return s;
+    if (grad && c->opt.mttkrp == GCP_MTTKRP_DETERMINISTIC) {
+        s = gcpk_det_grad(c, f, &blocks);
+        if (s) return s;
+    } else {
+        GCP_CUDA(c, gcpk::launch_fused(f, c->Abf != nullptr, c->max_blocks, c->st, &blocks));
+    }
+    if (stop) GCP_CUDA(c, cudaEventRecord(stop, c->st));
+    GCP_CUDA(c, gcpk::launch_finish_loss(c->partials, blocks, w_nz, w_z, c->dloss, c->status, c->st));
+    return GCP_OK;
+}
+
+gcp_status copy_grad_out(gcp_ctx *c, float *G_out) {
+    if (!G_out) return GCP_OK;
+    GCP_CUDA(c, cudaMemcpy2DAsync(G_out, (size_t)c->R * 4, c->G, (size_t)c->Rp * 4, (size_t)c->R * 4,
+                                  (size_t)c->total_rows, cudaMemcpyDefault, c->st));
+    return GCP_OK;
+}
+
+gcp_status read_loss(gcp_ctx *c, double *loss_out) {
+    GCP_CUDA(c, cudaMemcpyAsync(c->h_loss, c->dloss, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    gcp_status s = collect(c);
+    if (loss_out) *loss_out = c->h_loss[0];
+    return s;
+}
+
+gcp_status refresh_bf16(gcp_ctx *c) {
+    if (!c->Abf) return GCP_OK;
+    GCP_CUDA(c, gcpk::launch_to_bf16((int64_t)c->total_rows * c->Rp, c->A, c->Abf, c->st));
+    return GCP_OK;
+}
+
+}  // namespace
+
+// =================================================================== ABI
+extern "C" {
+
+void gcp_options_default(gcp_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->factor_dtype = GCP_FP32;
+    opt->mttkrp = GCP_MTTKRP_ATOMIC;
+    opt->sampling = GCP_SAMPLING_STRATIFIED;
+    opt->max_attempts = 64;
+    opt->hash_max_load = 0.3;
+}
+
+gcp_status gcp_create(int32_t ndim, const int64_t *dims, int64_t nnz, const int32_t *coords, const float *vals,
+                      int32_t rank, int32_t loss, const gcp_options *opt, gcp_ctx **out) {
+    if (!out) return fail(nullptr, GCP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nnz < 1 || !coords || !vals) return fail(nullptr, GCP_ERR_ARG, "need nnz >= 1, coords and vals");
+    if (opt && opt->sampling == GCP_SAMPLING_UNIFORM)
+        return fail(nullptr, GCP_ERR_ARG, "uniform sampling is for dense tensors (gcp_create_dense)");
+    // host checks of the nonzeros
+    if (ndim >= 2 && ndim <= GCP_MAX_NDIM && dims) {
+        for (int64_t e = 0; e < nnz; ++e) {
+            for (int k = 0; k < ndim; ++k) {
+                const int32_t v = coords[e * ndim + k];
+                if (v < 0 || v >= dims[k]) return fail(nullptr, GCP_ERR_ARG, "coordinate out of range");
+            }
+            const float x = vals[e];
+            if (!std::isfinite(x)) return fail(nullptr, GCP_ERR_ARG, "non-finite value");
+            if ((loss == GCP_POISSON && x < 0.0f) || (loss == GCP_GAMMA && x <= 0.0f) ||
+                (loss == GCP_BERNOULLI_LOGIT && x != 1.0f && x != 0.0f))
+                return fail(nullptr, GCP_ERR_DOMAIN, "value outside the loss's domain");
+        }
+    }
+    gcp_ctx *c = new (std::nothrow) gcp_ctx();
+    if (!c) return fail(nullptr, GCP_ERR_OOM, "host allocation");
+    gcp_status s = init_common(c, ndim, dims, rank, loss, opt);
+    if (s) {
+        destroy_buffers(c);
+        delete c;
+        return s;
+    }
+    if ((double)nnz > c->M) {
+        destroy_buffers(c);
+        delete c;
+        return fail(nullptr, GCP_ERR_ARG, "more nonzeros than cells");
+    }
+    c->nnz = nnz;
+    c->rec_words = gcpk::rec_words_for(ndim);
+    const uint64_t cap = next_pow2((uint64_t)std::ceil((double)nnz / c->opt.hash_max_load)) < 4
+                             ? 4
+                             : next_pow2((uint64_t)std::ceil((double)nnz / c->opt.hash_max_load));
+    c->hbmask = cap / 4 - 1;
+    int32_t *dcoords = nullptr;
+    float *dvals = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&c->rec, (size_t)nnz * c->rec_words * 4)) || (e = cudaMalloc(&c->hkeys, cap * 8)) ||
+        (e = cudaMalloc(&dcoords, (size_t)nnz * ndim * 4)) || (e = cudaMalloc(&dvals, (size_t)nnz * 4))) {
+        cudaFree(dcoords);
+        cudaFree(dvals);
+        destroy_buffers(c);
+        delete c;
+        return cuda_fail(nullptr, e, "allocating nonzero storage");
+    }
+    if ((e = cudaMemsetAsync(c->hkeys, 0xFF, cap * 8, c->st)) ||
+        (e = cudaMemcpyAsync(dcoords, coords, (size_t)nnz * ndim * 4, cudaMemcpyHostToDevice, c->st)) ||
+        (e = cudaMemcpyAsync(dvals, vals, (size_t)nnz * 4, cudaMemcpyHostToDevice, c->st)) ||
+        (e = gcpk::launch_build_records(dcoords, dvals, nnz, ndim, c->stride, c->rec_words, c->rec, c->hkeys,
+                                        c->hbmask, c->status, c->st)) ||
+        (e = cudaStreamSynchronize(c->st))) {
+        cudaFree(dcoords);
+        cudaFree(dvals);
+        destroy_buffers(c);
+        delete c;
+        return cuda_fail(nullptr, e, "building nonzero records");
+    }
+    cudaFree(dcoords);
+    cudaFree(dvals);
+    s = collect(c);
+    if (s) {
+        g_create_err = c->err;
+        destroy_buffers(c);
+        delete c;
+        return s;
+    }
+    *out = c;
+    return GCP_OK;
+}
+
+gcp_status gcp_create_dense(int32_t ndim, const int64_t *dims, const float *X, int32_t rank, int32_t loss,
+                            const gcp_options *opt, gcp_ctx **out) {
+    if (!out) return fail(nullptr, GCP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!X) return fail(nullptr, GCP_ERR_ARG, "X is NULL");
+    gcp_ctx *c = new (std::nothrow) gcp_ctx();
+    if (!c) return fail(nullptr, GCP_ERR_OOM, "host allocation");
+    gcp_options o;
+    gcp_options_default(&o);
+    if (opt) o = *opt;
+    o.sampling = GCP_SAMPLING_UNIFORM;
+    gcp_status s = init_common(c, ndim, dims, rank, loss, &o);
+    if (s) {
+        destroy_buffers(c);
+        delete c;
+        return s;
+    }
+    c->dense = true;
+    c->nnz = (int64_t)c->M;
+    const size_t bytes = (size_t)c->M * 4;
+    cudaError_t e;
+    if ((e = cudaMalloc(&c->X, bytes)) ||
+        (e = cudaMemcpyAsync(c->X, X, bytes, cudaMemcpyDefault, c->st)) || (e = cudaStreamSynchronize(c->st))) {
+        destroy_buffers(c);
+        delete c;
+        return cuda_fail(nullptr, e, "copying the dense tensor");
+    }
+    *out = c;
+    return GCP_OK;
+}
+
+void gcp_destroy(gcp_ctx *c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->st);
+    destroy_buffers(c);
+    delete c;
+}
+
+const char *gcp_last_error(const gcp_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+int32_t gcp_ndim(const gcp_ctx *c) { return c ? c->d : 0; }
+int32_t gcp_rank(const gcp_ctx *c) { return c ? c->R : 0; }
+int64_t gcp_nnz(const gcp_ctx *c) { return c ? c->nnz : 0; }
+int64_t gcp_num_params(const gcp_ctx *c) { return c ? c->total_rows * c->R : 0; }
+
+gcp_status gcp_set_factors(gcp_ctx *c, const float *A) {
+    if (!c || !A) return fail(c, GCP_ERR_ARG, "NULL argument");
+    DeviceGuard g(c->device);
+    GCP_CUDA(c, cudaMemcpy2DAsync(c->A, (size_t)c->Rp * 4, A, (size_t)c->R * 4, (size_t)c->R * 4,
+                                  (size_t)c->total_rows, cudaMemcpyDefault, c->st));
+    return refresh_bf16(c);
+}
+
+gcp_status gcp_set_factor(gcp_ctx *c, int32_t mode, const float *A_mode) {
+    if (!c || !A_mode) return fail(c, GCP_ERR_ARG, "NULL argument");
+    if (mode < 0 || mode >= c->d) return fail(c, GCP_ERR_ARG, "mode out of range");
+    DeviceGuard g(c->device);
+    GCP_CUDA(c, cudaMemcpy2DAsync(c->A + c->rowoff[mode] * c->Rp, (size_t)c->Rp * 4, A_mode, (size_t)c->R * 4,
+                                  (size_t)c->R * 4, (size_t)c->dims[mode], cudaMemcpyDefault, c->st));
+    return refresh_bf16(c);
+}
+
+gcp_status gcp_get_factors(gcp_ctx *c, float *A_out) {
+    if (!c || !A_out) return fail(c, GCP_ERR_ARG, "NULL argument");
+    DeviceGuard g(c->device);
+    GCP_CUDA(c, cudaMemcpy2DAsync(A_out, (size_t)c->R * 4, c->A, (size_t)c->Rp * 4, (size_t)c->R * 4,
+                                  (size_t)c->total_rows, cudaMemcpyDefault, c->st));
+    return collect(c);
+}
+
+gcp_status gcp_reset_adam(gcp_ctx *c) {
+    if (!c) return fail(c, GCP_ERR_ARG, "NULL context");
+    DeviceGuard g(c->device);
+    const size_t bytes = (size_t)c->total_rows * c->Rp * 4;
+    GCP_CUDA(c, cudaMemsetAsync(c->B, 0, bytes, c->st));
+    GCP_CUDA(c, cudaMemsetAsync(c->C, 0, bytes, c->st));
+    return GCP_OK;
+}
+
+gcp_status gcp_sample(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, int32_t *idx_out, float *x_out,
+                      float *w_out) {
+    if (!c) return fail(c, GCP_ERR_ARG, "NULL context");
+    DeviceGuard g(c->device);
+    gcp_status s = check_counts(c, p, q);
+    if (s) return s;
+    double w_nz, w_z;
+    weights(c, p, q, w_nz, w_z);
+    GCP_CUDA(c, gcpk::launch_sample(sample_spec(c, iter, p, q), idx_out, x_out, w_out, (float)w_nz, (float)w_z,
+                                    c->st));
+    return GCP_OK;
+}
+
+gcp_status gcp_loss(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, double *loss_out) {
+    if (!c || !loss_out) return fail(c, GCP_ERR_ARG, "NULL argument");
+    DeviceGuard g(c->device);
+    gcp_status s = run_fused(c, iter, p, q, false, nullptr);
+    if (s) return s;
+    return read_loss(c, loss_out);
+}
+
+gcp_status gcp_loss_async(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, double *dloss_out) {
+    if (!c || !dloss_out) return fail(c, GCP_ERR_ARG, "NULL argument");
+    DeviceGuard g(c->device);
+    gcp_status s = run_fused(c, iter, p, q, false, nullptr);
+    if (s) return s;
+    GCP_CUDA(c, cudaMemcpyAsync(dloss_out, c->dloss, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    return GCP_OK;
+}
+
+gcp_status gcp_grad(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, float *G_out, double *loss_out) {
+    if (!c) return fail(c, GCP_ERR_ARG, "NULL context");
+    DeviceGuard g(c->device);
+    gcp_status s = run_fused(c, iter, p, q, true, nullptr);
+    if (s) return s;
+    s = copy_grad_out(c, G_out);
+    if (s) return s;
+    return loss_out ? read_loss(c, loss_out) : GCP_OK;
+}
+
+gcp_status gcp_grad_async(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, const float *dscale, float *G_out,
+                          double *dloss_out) {
+    if (!c) return fail(c, GCP_ERR_ARG, "NULL context");
+    DeviceGuard g(c->device);
+    gcp_status s = run_fused(c, iter, p, q, true, dscale);
+    if (s) return s;
+    s = copy_grad_out(c, G_out);
+    if (s) return s;
+    if (dloss_out)
+        GCP_CUDA(c, cudaMemcpyAsync(dloss_out, c->dloss, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    return GCP_OK;
+}
+
+gcp_status gcp_adam_step(gcp_ctx *c, const gcp_adam_params *prm, int64_t t) {
+    if (!c || !prm) return fail(c, GCP_ERR_ARG, "NULL argument");
+    if (t < 1) return fail(c, GCP_ERR_ARG, "Adam step t must be >= 1");
+    if (!(prm->beta1 >= 0.0 && prm->beta1 < 1.0 && prm->beta2 >= 0.0 && prm->beta2 < 1.0 && prm->eps >= 0.0))
+        return fail(c, GCP_ERR_ARG, "Adam parameters out of range");
+    DeviceGuard g(c->device);
+    const double c1 = 1.0 - std::pow(prm->beta1, (double)t), c2 = 1.0 - std::pow(prm->beta2, (double)t);
+    GCP_CUDA(c, gcpk::launch_adam((int64_t)c->total_rows * c->Rp, c->Rp, c->R, c->A, c->B, c->C, c->G,
+                                  (float)prm->lr, (float)prm->beta1, (float)prm->beta2, (float)(1.0 / c1),
+                                  (float)(1.0 / c2), (float)prm->eps, (float)prm->lower, c->Abf, c->st));
+    return GCP_OK;
+}
+
+gcp_status gcp_sync(gcp_ctx *c) {
+    if (!c) return fail(c, GCP_ERR_ARG, "NULL context");
+    DeviceGuard g(c->device);
+    return collect(c);
+}
+
+gcp_status gcp_fit(gcp_ctx *c, const gcp_fit_params *prm, gcp_fit_report *rep) {
+    if (!c || !prm) return fail(c, GCP_ERR_ARG, "NULL argument");
+    if (prm->iters < 1 || prm->max_epochs < 0 || prm->max_fails < 1 || !(prm->decay > 0.0))
+        return fail(c, GCP_ERR_ARG, "bad fit parameters");
+    DeviceGuard g(c->device);
+    const size_t bytes = (size_t)c->total_rows * c->Rp * 4;
+    if (!c->bk_A) {
+        cudaError_t e;
+        if ((e = cudaMalloc(&c->bk_A, bytes)) || (e = cudaMalloc(&c->bk_B, bytes)) ||
+            (e = cudaMalloc(&c->bk_C, bytes)))
+            return cuda_fail(c, e, "allocating fit backups");
+    }
+    gcp_fit_report r;
+    std::memset(&r, 0, sizeof(r));
+    const auto t0 = std::chrono::steady_clock::now();
+    auto objective = [&](double &F) -> gcp_status {
+        gcp_status s = run_fused(c, GCP_ITER_OBJECTIVE, prm->p_obj, prm->q_obj, false, nullptr);
+        if (s) return s;
+        s = read_loss(c, &F);
+        r.attempts_per_zero = prm->q_obj > 0 ? c->h_loss[1] / (double)prm->q_obj : 0.0;
+        return s;
+    };
+    auto backup = [&](bool save) -> gcp_status {
+        float *src[3] = {c->A, c->B, c->C}, *dst[3] = {c->bk_A, c->bk_B, c->bk_C};
+        for (int i = 0; i < 3; ++i)
+            GCP_CUDA(c, cudaMemcpyAsync(save ? dst[i] : src[i], save ? src[i] : dst[i], bytes,
+                                        cudaMemcpyDeviceToDevice, c->st));
+        return save ? GCP_OK : refresh_bf16(c);
+    };
+    double F = 0.0;
+    gcp_status s = objective(F);
+    if (s) return s;
+    r.objective0 = F;
+    double Fbest = F;
+    int64_t t = 0, t_saved = 0, steps_run = 0;
+    gcp_adam_params adam = prm->adam;
+    uint64_t iter = prm->iter0;
+    if ((s = backup(true))) return s;
+    for (int epoch = 0; epoch < prm->max_epochs; ++epoch) {
+        for (int it = 0; it < prm->iters; ++it) {
+            if ((s = run_fused(c, iter++, prm->p, prm->q, true, nullptr))) return s;
+            if ((s = gcp_adam_step(c, &adam, t + 1))) return s;
+            ++t;
+            ++steps_run;
+        }
+        if ((s = objective(F))) return s;
+        if (epoch < GCP_FIT_TRACE) r.trace[epoch] = F;
+        r.epochs = epoch + 1;
+        if (!(F < Fbest)) {  // failed epoch: restore and decay the rate
+            if ((s = backup(false))) return s;
+            t = t_saved;
+            adam.lr *= prm->decay;
+            if (++r.fails >= prm->max_fails) break;
+        } else {
+            Fbest = F;
+            t_saved = t;
+            if ((s = backup(true))) return s;
+        }
+    }
+    GCP_CUDA(c, cudaStreamSynchronize(c->st));
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    r.iterations = t;
+    r.objective = Fbest;
+    r.lr = adam.lr;
+    r.grad_samples_per_s = r.seconds > 0 ? (double)(prm->p + prm->q) * (double)steps_run / r.seconds : 0.0;
+    if (rep) *rep = r;
+    return GCP_OK;
+}
+
+gcp_status gcp_profile(gcp_ctx *c, int32_t enable) {
+    if (!c) return fail(c, GCP_ERR_ARG, "NULL context");
+    c->prof = enable != 0;
+    return GCP_OK;
+}
+
+gcp_status gcp_profile_read(gcp_ctx *c, double *kernel_ms, int64_t *launches) {
+    if (!c || !kernel_ms || !launches) return fail(c, GCP_ERR_ARG, "NULL argument");
+    DeviceGuard g(c->device);
+    GCP_CUDA(c, cudaStreamSynchronize(c->st));
+    double total = 0.0;
+    for (size_t i = 0; i < c->prof_used; ++i) {
+        float ms = 0.0f;
+        GCP_CUDA(c, cudaEventElapsedTime(&ms, c->prof_ev[i].first, c->prof_ev[i].second));
+        total += ms;
+    }
+    *kernel_ms = total;
+    *launches = (int64_t)c->prof_used;
+    c->prof_used = 0;
+    return GCP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,418 @@
+// gcp_kernels.cu -- the fused stochastic GCP gradient on sm_103a.
+//
+// One pass per sample set (the fused Sampling-MTTKRP of Sec. 3.1.2, here with
+// stratified sampling and hash rejection):
+//   phase A, one sample per lane: Philox4x64-10 counters -> nonzero record
+//            load, or zero candidates probed against the nonzero hash set
+//            until one is absent (Sec. 3.1.1);
+//   phase B, one sample per group of L = Rp / (16 B / elt) lanes: each lane
+//            gathers a 16-byte slice of the d factor rows, forms the CP model
+//            entry m (Eq. cp) with a shuffle reduction over the group,
+//            evaluates f and f', and scatters w f' prod_{k!=n} A_k(i_k,:)
+//            into every mode's gradient row with FP32 vector reductions
+//            (Eq. gcp-gradient, atomic MTTKRP of Sec. 3.1.2).
+// The sampled loss is accumulated in FP64 per lane, reduced per block into
+// a partials array and finished by a single-block kernel in fixed order.
+#include <cuda_bf16.h>
+
+#include "gcp_device.cuh"
+#include "gcp_internal.h"
+
+using namespace gcpdev;
+
+namespace gcpk {
+
+constexpr int kThreads = 256;
+
+template <int D>
+__device__ __forceinline__ void draw_tuple(const SampleSpec &S, uint64_t stream, uint64_t j, uint64_t sub0,
+                                           int32_t (&idx)[D]) {
+#pragma unroll
+    for (int b = 0; 4 * b < D; ++b) {
+        const U64x4 w = philox4x64_10(j, sub0 + (uint64_t)b, S.iter, 0, S.seed, stream);
+#pragma unroll
+        for (int k = 4 * b; k < D && k < 4 * b + 4; ++k)
+            idx[k] = (int32_t)map_range(w.v[k - 4 * b], (uint64_t)S.dims[k]);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ uint64_t linear_of(const SampleSpec &S, const int32_t (&idx)[D]) {
+    uint64_t L = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) L += (uint64_t)idx[k] * S.stride[k];
+    return L;
+}
+
+template <int D>
+__device__ __forceinline__ void load_record(const int32_t *__restrict__ rec, uint64_t e, int32_t (&idx)[D],
+                                            float &x) {
+    constexpr int NV = (D + 4) / 4;  // 16-byte vectors holding D coordinates + value
+    constexpr int RW = rec_words_for(D);
+    const int4 *r = reinterpret_cast<const int4 *>(rec + e * RW);
+    int w[4 * NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const int4 t = __ldg(r + v);
+        w[4 * v] = t.x;
+        w[4 * v + 1] = t.y;
+        w[4 * v + 2] = t.z;
+        w[4 * v + 3] = t.w;
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) idx[k] = w[k];
+    x = __int_as_float(w[D]);
+}
+
+// Draw sample s of the set.  Returns false when the sample does not exist
+// (exhausted zero draw); idx then holds the last candidate.
+template <int D>
+__device__ __forceinline__ bool draw_sample(const SampleSpec &S, int64_t s, int32_t (&idx)[D], float &x,
+                                            int &attempts) {
+    if (S.sampling == GCP_SAMPLING_UNIFORM) {
+        draw_tuple<D>(S, kStreamUniform, (uint64_t)s, 0, idx);
+        x = __ldg(S.dense + linear_of<D>(S, idx));
+        return true;
+    }
+    if (s < S.p) {
+        const U64x4 w = philox4x64_10((uint64_t)s, 0, S.iter, 0, S.seed, kStreamNonzero);
+        load_record<D>(S.rec, map_range(w.v[0], (uint64_t)S.nnz), idx, x);
+        return true;
+    }
+    const uint64_t j = (uint64_t)(s - S.p);
+    x = 0.0f;
+    if (S.sampling == GCP_SAMPLING_SEMI_STRATIFIED) {
+        draw_tuple<D>(S, kStreamSemiZero, j, 0, idx);
+        return true;
+    }
+    for (int a = 0; a < S.max_attempts; ++a) {
+        draw_tuple<D>(S, kStreamZero, j, 4 * (uint64_t)a, idx);
+        const int h = hash_contains(S.hkeys, S.hbmask, linear_of<D>(S, idx));
+        if (h == 0) {
+            attempts += a + 1;
+            return true;
+        }
+        if (h < 0) {
+            atomicOr(S.status, kErrHashFull);
+            return false;
+        }
+    }
+    attempts += S.max_attempts;
+    atomicOr(S.status, kErrExhausted);
+    return false;
+}
+
+// ------------------------------------------------------------ fused pass
+template <int D, typename TF>
+__global__ void __launch_bounds__(kThreads) k_fused(const FusedSpec P) {
+    constexpr int VEC = Vec<TF>::N;
+    const int lane = threadIdx.x & 31;
+    const int log2L = P.log2L;
+    const int L = 1 << log2L;
+    const int glane = lane & (L - 1);
+    const int grp = lane >> log2L;
+    const int ngrp = 32 >> log2L;
+    const unsigned gmask = (L == 32) ? 0xFFFFFFFFu : (((1u << L) - 1u) << (grp * L));
+    const int64_t S = P.s.p + P.s.q;
+    const int64_t ntiles = (S + 31) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const TF *__restrict__ F = static_cast<const TF *>(P.F);
+    const float scale = P.dscale ? __ldg(P.dscale) : 1.0f;
+    const bool semi = P.s.sampling == GCP_SAMPLING_SEMI_STRATIFIED;
+
+    double acc_nz = 0.0, acc_z = 0.0;
+    int attempts = 0;
+
+    for (int64_t tile = warp0; tile < ntiles; tile += nwarps) {
+        // phase A: one sample per lane
+        const int64_t s_mine = (tile << 5) + lane;
+        int32_t idx[D] = {};
+        float x = 0.0f;
+        bool ok = false;
+        if (s_mine < S) ok = draw_sample<D>(P.s, s_mine, idx, x, attempts);
+
+        // phase B: one sample per group of L lanes
+        for (int it = 0; it < L; ++it) {
+            const int src = it * ngrp + grp;
+            int32_t ii[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) ii[k] = __shfl_sync(0xFFFFFFFFu, idx[k], src);
+            const float xs = __shfl_sync(0xFFFFFFFFu, x, src);
+            const int oks = __shfl_sync(0xFFFFFFFFu, (int)ok, src);
+            if (!oks) continue;  // uniform within the group
+            const bool is_nz = ((tile << 5) + src) < P.s.p;
+
+            float a[D][VEC];
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                Vec<TF>::load(F + (P.rowoff[k] + ii[k]) * (int64_t)P.Rp + glane * VEC, a[k]);
+            // suffix products suf[k] = prod_{j>k} a_j
+            float suf[D][VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) suf[D - 1][v] = 1.0f;
+#pragma unroll
+            for (int k = D - 2; k >= 0; --k)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) suf[k][v] = suf[k + 1][v] * a[k + 1][v];
+            float m = 0.0f;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) m += a[0][v] * suf[0][v];
+            for (int o = L >> 1; o > 0; o >>= 1) m += __shfl_xor_sync(gmask, m, o);
+
+            float f, df;
+            loss_eval(P.loss, xs, m, f, df);
+            if (semi && is_nz) {
+                float f0, df0;
+                loss_eval(P.loss, 0.0f, m, f0, df0);
+                f -= f0;
+                df -= df0;
+            }
+            if (glane == 0) {
+                if (is_nz)
+                    acc_nz += (double)f;
+                else
+                    acc_z += (double)f;
+            }
+            if (P.G) {
+                const float y = (is_nz ? P.w_nz : P.w_z) * df * scale;
+                float pre[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) pre[v] = y;
+#pragma unroll
+                for (int n = 0; n < D; ++n) {
+                    float *g = P.G + (P.rowoff[n] + ii[n]) * (int64_t)P.Rp + glane * VEC;
+#pragma unroll
+                    for (int h = 0; h < VEC; h += 4)
+                        red_add_v4(g + h, pre[h] * suf[n][h], pre[h + 1] * suf[n][h + 1],
+                                   pre[h + 2] * suf[n][h + 2], pre[h + 3] * suf[n][h + 3]);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) pre[v] *= a[n][v];
+                }
+            }
+        }
+    }
+
+    // block reduction of the FP64 loss sums and attempt counts
+    double att = (double)attempts;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc_nz += __shfl_xor_sync(0xFFFFFFFFu, acc_nz, o);
+        acc_z += __shfl_xor_sync(0xFFFFFFFFu, acc_z, o);
+        att += __shfl_xor_sync(0xFFFFFFFFu, att, o);
+    }
+    __shared__ double red[3][kThreads / 32];
+    const int warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = acc_nz;
+        red[1][warp] = acc_z;
+        red[2][warp] = att;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += red[threadIdx.x][w];
+        P.partials[4 * blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+// Fixed-order reduction of the block partials (one block).
+__global__ void __launch_bounds__(kThreads) k_finish_loss(const double *__restrict__ partials, int nblocks,
+                                                         double w_nz, double w_z, double *dloss, int *status) {
+    __shared__ double sh[3][kThreads];
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += kThreads)
+        for (int c = 0; c < 3; ++c) t[c] += partials[4 * b + c];
+    for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] = t[c];
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double loss = w_nz * sh[0][0] + w_z * sh[1][0];
+        dloss[0] = loss;
+        dloss[1] = sh[2][0];
+        if (!isfinite(loss)) atomicOr(status, kErrNonfinite);
+    }
+}
+
+// ------------------------------------------------------------- sampling
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_sample(const SampleSpec S, int32_t *idx_out, float *x_out,
+                                                    float *w_out, float w_nz, float w_z) {
+    const int64_t n = S.p + S.q;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        int32_t idx[D];
+        float x = 0.0f;
+        int att = 0;
+        draw_sample<D>(S, s, idx, x, att);
+        if (idx_out)
+#pragma unroll
+            for (int k = 0; k < D; ++k) idx_out[s * D + k] = idx[k];
+        if (x_out) x_out[s] = x;
+        if (w_out) w_out[s] = s < S.p ? w_nz : w_z;
+    }
+}
+
+// ------------------------------------------------------ nonzero records
+__global__ void k_build_records(const int32_t *__restrict__ coords, const float *__restrict__ vals, int64_t nnz,
+                                int d, SampleSpec S, int rec_words, int32_t *rec, uint64_t *hkeys,
+                                uint64_t hbmask, int *status) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t L = 0;
+        int32_t *r = rec + e * rec_words;
+        for (int k = 0; k < d; ++k) {
+            const int32_t c = coords[e * d + k];
+            r[k] = c;
+            L += (uint64_t)c * S.stride[k];
+        }
+        r[d] = __float_as_int(vals[e]);
+        for (int k = d + 1; k < rec_words; ++k) r[k] = 0;
+        const int rc = hash_insert(hkeys, hbmask, L);
+        if (rc) atomicOr(status, rc);
+    }
+}
+
+// ------------------------------------------------------------------ Adam
+// Algorithm 1 on the flat parameter vector (Sec. 3.1.3); padded columns
+// (col >= R) stay zero.  With BF16 storage the kernel-read copy is refreshed.
+__global__ void k_adam(int64_t n, int Rp, int R, float *__restrict__ A, float *__restrict__ B,
+                       float *__restrict__ C, const float *__restrict__ G, float lr, float beta1, float beta2,
+                       float c1inv, float c2inv, float eps, float lower, __nv_bfloat16 *Abf) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        if ((int)(e % Rp) >= R) continue;
+        const float g = G[e];
+        const float b = beta1 * B[e] + (1.0f - beta1) * g;
+        const float c = beta2 * C[e] + (1.0f - beta2) * g * g;
+        B[e] = b;
+        C[e] = c;
+        float a = A[e] - lr * ((b * c1inv) / sqrtf(c * c2inv + eps));
+        a = fmaxf(a, lower);
+        A[e] = a;
+        if (Abf) Abf[e] = __float2bfloat16_rn(a);
+    }
+}
+
+__global__ void k_to_bf16(int64_t n, const float *__restrict__ A, __nv_bfloat16 *Abf) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        Abf[e] = __float2bfloat16_rn(A[e]);
+}
+
+// --------------------------------------------------------------- launches
+static int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return sms;
+}
+
+static int elementwise_blocks(int64_t n) {
+    const int64_t want = (n + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)num_sms() * 8;
+    return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+cudaError_t launch_build_records(const int32_t *coords, const float *vals, int64_t nnz, int d,
+                                 const uint64_t *stride, int rec_words, int32_t *rec, uint64_t *hkeys,
+                                 uint64_t hbmask, int *status, cudaStream_t st) {
+    SampleSpec S{};
+    S.d = d;
+    for (int k = 0; k < d; ++k) S.stride[k] = stride[k];
+    k_build_records<<<elementwise_blocks(nnz), kThreads, 0, st>>>(coords, vals, nnz, d, S, rec_words, rec, hkeys,
+                                                                   hbmask, status);
+    return cudaGetLastError();
+}
+
+#define GCP_DISPATCH_D(d, MACRO) \
+    switch (d) {                 \
+    case 2: MACRO(2); break;     \
+    case 3: MACRO(3); break;     \
+    case 4: MACRO(4); break;     \
+    case 5: MACRO(5); break;     \
+    case 6: MACRO(6); break;     \
+    case 7: MACRO(7); break;     \
+    case 8: MACRO(8); break;     \
+    default: return cudaErrorInvalidValue; \
+    }
+
+cudaError_t launch_sample(const SampleSpec &s, int32_t *idx_out, float *x_out, float *w_out, float w_nz,
+                          float w_z, cudaStream_t st) {
+    const int64_t n = s.p + s.q;
+    if (n == 0) return cudaSuccess;
+    const int blocks = elementwise_blocks(n);
+#define GCP_LAUNCH_SAMPLE(D) k_sample<D><<<blocks, kThreads, 0, st>>>(s, idx_out, x_out, w_out, w_nz, w_z)
+    GCP_DISPATCH_D(s.d, GCP_LAUNCH_SAMPLE)
+#undef GCP_LAUNCH_SAMPLE
+    return cudaGetLastError();
+}
+
+template <int D, typename TF>
+static int occupancy_blocks() {
+    static int nb = -1;
+    if (nb < 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<D, TF>, kThreads, 0);
+        nb = (per_sm < 1 ? 1 : per_sm) * num_sms();
+    }
+    return nb;
+}
+
+int fused_max_blocks(int d, bool bf16) {
+    int nb = 0;
+#define GCP_OCC(D) nb = bf16 ? occupancy_blocks<D, __nv_bfloat16>() : occupancy_blocks<D, float>()
+    switch (d) {
+    case 2: GCP_OCC(2); break;
+    case 3: GCP_OCC(3); break;
+    case 4: GCP_OCC(4); break;
+    case 5: GCP_OCC(5); break;
+    case 6: GCP_OCC(6); break;
+    case 7: GCP_OCC(7); break;
+    case 8: GCP_OCC(8); break;
+    default: nb = num_sms();
+    }
+#undef GCP_OCC
+    return nb;
+}
+
+cudaError_t launch_fused(const FusedSpec &f, bool bf16, int max_blocks, cudaStream_t st, int *blocks_used) {
+    const int64_t S = f.s.p + f.s.q;
+    const int64_t ntiles = (S + 31) / 32;
+    int64_t want = (ntiles + (kThreads / 32) - 1) / (kThreads / 32);
+    if (want < 1) want = 1;
+    const int blocks = (int)(want < max_blocks ? want : max_blocks);
+    *blocks_used = blocks;
+#define GCP_LAUNCH_FUSED(D)                                                 \
+    if (bf16)                                                               \
+        k_fused<D, __nv_bfloat16><<<blocks, kThreads, 0, st>>>(f);          \
+    else                                                                    \
+        k_fused<D, float><<<blocks, kThreads, 0, st>>>(f)
+    GCP_DISPATCH_D(f.s.d, GCP_LAUNCH_FUSED)
+#undef GCP_LAUNCH_FUSED
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_loss(const double *partials, int nblocks, double w_nz, double w_z, double *dloss,
+                               int *status, cudaStream_t st) {
+    k_finish_loss<<<1, kThreads, 0, st>>>(partials, nblocks, w_nz, w_z, dloss, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(int64_t n, int Rp, int R, float *A, float *B, float *C, const float *G, float lr,
+                        float beta1, float beta2, float c1inv, float c2inv, float eps, float lower, void *Abf,
+                        cudaStream_t st) {
+    k_adam<<<elementwise_blocks(n), kThreads, 0, st>>>(n, Rp, R, A, B, C, G, lr, beta1, beta2, c1inv, c2inv, eps,
+                                                        lower, static_cast<__nv_bfloat16 *>(Abf));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(int64_t n, const float *A, void *Abf, cudaStream_t st) {
+    k_to_bf16<<<elementwise_blocks(n), kThreads, 0, st>>>(n, A, static_cast<__nv_bfloat16 *>(Abf));
+    return cudaGetLastError();
+}
+
+}  // namespace gcpk

@@ -221,3 +221,25 @@ def workload_zipf_count(scale=1.0, seed=1002):
     S = max(256, int((1 << 20) * scale))
     return dict(dims=dims, coords=coords, vals=vals, rank=32, loss="poisson",
                 factors=factors_uniform(dims, 32, seed + 1000), p=S, q=S)
+
+
+def cached(name, make, cache_dir=None):
+    """Return make()'s dict of arrays and scalars, stored once under
+    `cache_dir` (default: <repo>/_cache, or $GCP_CACHE_DIR) as a pickle so that
+    several processes of one run generate a large workload only once."""
+    import os
+    import pickle
+
+    d = cache_dir or os.environ.get("GCP_CACHE_DIR") or os.path.join(
+        os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_cache")
+    path = os.path.join(d, name + ".pkl")
+    if os.path.exists(path):
+        with open(path, "rb") as f:
+            return pickle.load(f)
+    w = make()
+    os.makedirs(d, exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "wb") as f:
+        pickle.dump(w, f, protocol=pickle.HIGHEST_PROTOCOL)
+    os.replace(tmp, path)
+    return w

@@ -20,6 +20,8 @@ def gpu_lib():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_2605_20353_gb300 as gcp
+    from paper_2605_20353_gb300 import build
 
+    build.build()
     gcp.load()  # raises if the CUDA library is missing: no fallback
     return gcp

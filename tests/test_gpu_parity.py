@@ -1,0 +1,324 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Sampled indices must match bit for bit; the sampled loss and every mode's
+gradient must match within relative Frobenius error 1e-5 with FP32 factors
+and 5e-3 with BF16 factors.  Sizes span many 32-sample tiles with ragged
+tails; edge cases cover empty sample sets, exhausted zero draws, duplicates
+and every supported order and rank class.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-5
+TOL_BF16 = 5e-3
+
+
+def rel_err(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def split(flat, dims, R):
+    out, o = [], 0
+    for I in dims:
+        out.append(flat[o:o + I * R].reshape(I, R))
+        o += I * R
+    return out
+
+
+def bf16_round(a):
+    """Round-to-nearest-even of FP32 values to BF16, widened back to FP32."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def problem(dims, nnz, R, loss, seed):
+    coords, vals = synth.uniform_sparse(dims, nnz, seed, lam=2.0)
+    if loss == "bernoulli":
+        vals = np.ones_like(vals)
+    if loss in ("gaussian", "bernoulli"):
+        factors = synth.factors_normal(dims, R, seed + 1, std=0.6)
+    else:
+        factors = synth.factors_uniform(dims, R, seed + 1, lo=0.1, hi=1.0)
+    return coords, vals, factors
+
+
+def gpu_grad(gcp, torch, ctx, t, p, q):
+    G = torch.zeros(ctx.num_params, dtype=torch.float32, device="cuda")
+    loss, _ = ctx.grad(t, p, q, G_out=G)
+    return loss, G.cpu().numpy()
+
+
+def check_grad(gcp, torch, dims, coords, vals, R, loss, factors, p, q, t=0, seed=77, dtype="fp32", tol=TOL_FP32,
+               sampling="stratified"):
+    ctx = gcp.gcp_create(dims, coords, vals, R, loss, dtype=dtype, seed=seed, sampling=sampling)
+    ctx.set_factors(factors)
+    Lg, Gg = gpu_grad(gcp, torch, ctx, t, p, q)
+    fac = [bf16_round(a) for a in factors] if dtype == "bf16" else factors
+    if sampling == "semi":
+        idx, x, w, semi = oracle.semi_stratified_samples(seed, t, p, q, dims, coords, vals)
+    else:
+        idx, x, w, _ = oracle.stratified_samples(seed, t, p, q, dims, coords, vals)
+        semi = None
+    Lo, Go = oracle.sampled_loss_grad(dims, fac, loss, idx, x, w, semi=semi)
+    assert abs(Lg - Lo) <= tol * abs(Lo), (Lg, Lo)
+    for n, (a, b) in enumerate(zip(split(Gg, dims, R), Go)):
+        assert rel_err(a, b) <= tol, (n, rel_err(a, b))
+    ctx.close()
+    return Lg, Gg
+
+
+@pytest.fixture(scope="module")
+def env(gpu_lib):
+    import torch
+
+    return gpu_lib, torch
+
+
+# ------------------------------------------------------------- sampling
+@pytest.mark.parametrize("t", [0, 1, 7, 2**64 - 1])
+def test_sample_bit_exact_small(env, t):
+    gcp, torch = env
+    w = synth.workload_small_gaussian()
+    ctx = gcp.gcp_create(w["dims"], w["coords"], w["vals"], 4, "gaussian", seed=3001)
+    idx, x, wt = ctx.sample(t, 1000, 1000)
+    ido, xo, wo, _ = oracle.stratified_samples(3001, t, 1000, 1000, w["dims"], w["coords"], w["vals"])
+    assert np.array_equal(idx.cpu().numpy(), ido)
+    assert np.array_equal(x.cpu().numpy(), xo.astype(np.float32))
+    assert np.array_equal(wt.cpu().numpy(), wo.astype(np.float32))
+    ctx.close()
+
+
+def test_sample_bit_exact_zipf_4way(env):
+    gcp, torch = env
+    w = synth.workload_zipf_count(scale=0.01)
+    ctx = gcp.gcp_create(w["dims"], w["coords"], w["vals"], 32, "poisson", seed=3002)
+    p, q = w["p"] + 13, w["q"] + 5  # ragged tail
+    idx, x, _ = ctx.sample(3, p, q)
+    ido, xo, _, _ = oracle.stratified_samples(3002, 3, p, q, w["dims"], w["coords"], w["vals"])
+    assert np.array_equal(idx.cpu().numpy(), ido)
+    assert np.array_equal(x.cpu().numpy(), xo.astype(np.float32))
+    ctx.close()
+
+
+@pytest.mark.parametrize("d", [2, 5, 8])
+def test_sample_bit_exact_orders(env, d):
+    gcp, torch = env
+    dims = [7, 5, 9, 3, 4, 6, 2, 5][:d]
+    coords, vals, _ = problem(dims, min(300, int(np.prod(dims)) // 3), 4, "poisson", 90 + d)
+    ctx = gcp.gcp_create(dims, coords, vals, 4, "poisson", seed=11)
+    idx, x, _ = ctx.sample(2, 555, 999)
+    ido, xo, _, _ = oracle.stratified_samples(11, 2, 555, 999, dims, coords, vals)
+    assert np.array_equal(idx.cpu().numpy(), ido)
+    ctx.close()
+
+
+def test_sample_semi_and_dense_bit_exact(env):
+    gcp, torch = env
+    w = synth.workload_small_gaussian()
+    ctx = gcp.gcp_create(w["dims"], w["coords"], w["vals"], 4, "gaussian", seed=5, sampling="semi")
+    idx, x, wt = ctx.sample(4, 300, 700)
+    ido, xo, wo, _ = oracle.semi_stratified_samples(5, 4, 300, 700, w["dims"], w["coords"], w["vals"])
+    assert np.array_equal(idx.cpu().numpy(), ido)
+    assert np.array_equal(wt.cpu().numpy(), wo.astype(np.float32))
+    ctx.close()
+    dims = [6, 5, 4, 3, 7]
+    X = synth.dense_cp_sinusoid(dims, 4, rank_true=3)
+    ctx = gcp.gcp_create_dense(dims, X, 8, "gaussian", seed=9)
+    idx, x, wt = ctx.sample(1, 2049, 0)
+    ido, xo, wo = oracle.uniform_samples(9, 1, 2049, dims, X)
+    assert np.array_equal(idx.cpu().numpy(), ido)
+    assert np.array_equal(x.cpu().numpy(), xo.astype(np.float32))
+    ctx.close()
+
+
+# --------------------------------------------------------- loss + grad
+@pytest.mark.parametrize("loss", ["gaussian", "poisson", "bernoulli", "gamma"])
+def test_grad_fp32_all_losses(env, loss):
+    gcp, torch = env
+    dims = [50, 40, 30]
+    coords, vals, factors = problem(dims, 2000, 16, loss, 200)
+    check_grad(gcp, torch, dims, coords, vals, 16, loss, factors, 1234, 777, t=3)
+
+
+@pytest.mark.parametrize("d,R", [(2, 1), (3, 3), (4, 32), (5, 16), (6, 8), (8, 5), (3, 64), (3, 128), (4, 33)])
+def test_grad_orders_and_ranks(env, d, R):
+    gcp, torch = env
+    dims = [23, 17, 11, 7, 5, 6, 4, 3][:d]
+    coords, vals, factors = problem(dims, min(900, int(np.prod(dims)) // 4), R, "poisson", 300 + d * 7 + R)
+    check_grad(gcp, torch, dims, coords, vals, R, "poisson", factors, 1500, 1001, t=1)
+
+
+@pytest.mark.parametrize("loss", ["poisson", "bernoulli"])
+def test_grad_bf16(env, loss):
+    gcp, torch = env
+    dims = [60, 50, 40]
+    coords, vals, factors = problem(dims, 3000, 64, loss, 400)
+    Lg, Gg = check_grad(gcp, torch, dims, coords, vals, 64, loss, factors, 2000, 2000, dtype="bf16", tol=1e-5)
+    # against the FP32 factors: storage error, stated by the BF16 tolerance
+    idx, x, w, _ = oracle.stratified_samples(77, 0, 2000, 2000, dims, coords, vals)
+    Lo, Go = oracle.sampled_loss_grad(dims, factors, loss, idx, x, w)
+    assert abs(Lg - Lo) <= TOL_BF16 * abs(Lo)
+    assert rel_err(Gg, np.concatenate([g.ravel() for g in Go])) <= TOL_BF16
+
+
+def test_grad_semi_stratified(env):
+    gcp, torch = env
+    dims = [40, 30, 20]
+    coords, vals, factors = problem(dims, 1500, 8, "poisson", 500)
+    check_grad(gcp, torch, dims, coords, vals, 8, "poisson", factors, 999, 1501, sampling="semi")
+
+
+def test_grad_dense_uniform(env):
+    gcp, torch = env
+    dims = [10, 9, 8, 4, 5]
+    X = synth.dense_cp_sinusoid(dims, 21, rank_true=4)
+    factors = synth.factors_normal(dims, 16, 22, std=0.5)
+    ctx = gcp.gcp_create_dense(dims, X, 16, "gaussian", seed=4)
+    ctx.set_factors(factors)
+    Lg, Gg = gpu_grad(gcp, torch, ctx, 2, 5000, 0)
+    idx, x, w = oracle.uniform_samples(4, 2, 5000, dims, X)
+    Lo, Go = oracle.sampled_loss_grad(dims, factors, "gaussian", idx, x, w)
+    assert abs(Lg - Lo) <= TOL_FP32 * abs(Lo)
+    assert rel_err(Gg, np.concatenate([g.ravel() for g in Go])) <= TOL_FP32
+    ctx.close()
+
+
+def test_loss_only_call_matches_grad_call(env):
+    gcp, torch = env
+    w = synth.workload_small_gaussian()
+    ctx = gcp.gcp_create(w["dims"], w["coords"], w["vals"], 4, "gaussian", seed=1)
+    ctx.set_factors(w["factors"])
+    L1 = ctx.loss_value(5, 800, 900)
+    L2, _ = ctx.grad(5, 800, 900)
+    assert L1 == L2  # same sample set, same fixed-order reduction
+    ctx.close()
+
+
+def test_grad_scale_and_async_loss(env):
+    gcp, torch = env
+    w = synth.workload_small_gaussian()
+    ctx = gcp.gcp_create(w["dims"], w["coords"], w["vals"], 4, "gaussian", seed=1)
+    ctx.set_factors(w["factors"])
+    G1 = torch.zeros(ctx.num_params, device="cuda")
+    G2 = torch.zeros(ctx.num_params, device="cuda")
+    dl = torch.zeros(1, dtype=torch.float64, device="cuda")
+    L, _ = ctx.grad(2, 500, 500, G_out=G1)
+    ctx.grad_async(2, 500, 500, dscale=torch.tensor([-2.5], device="cuda"), G_out=G2, dloss=dl)
+    ctx.sync()
+    assert dl.item() == L
+    assert torch.allclose(G2, -2.5 * G1, rtol=1e-6, atol=0)
+    ctx.close()
+
+
+# ---------------------------------------------------------------- Adam
+def test_adam_step_parity(env):
+    gcp, torch = env
+    dims = [30, 20, 10]
+    coords, vals, factors = problem(dims, 800, 8, "poisson", 600)
+    ctx = gcp.gcp_create(dims, coords, vals, 8, "poisson", seed=3)
+    ctx.set_factors(factors)
+    A = oracle.flat_factors(factors)
+    B, C = np.zeros_like(A), np.zeros_like(A)
+    prm = gcp.AdamParams(lr=0.01, beta1=0.9, beta2=0.999, eps=1e-8, lower=0.0)
+    for t in range(1, 4):
+        ctx.grad(t, 500, 500, want_loss=False)
+        ctx.adam_step(prm, t)
+        idx, x, w, _ = oracle.stratified_samples(3, t, 500, 500, dims, coords, vals)
+        _, Go = oracle.sampled_loss_grad(dims, split(A, dims, 8), "poisson", idx, x, w)
+        oracle.adam_step(A, B, C, np.concatenate([g.ravel() for g in Go]), 0.01, 0.9, 0.999, 1e-8, 0.0, t)
+        Ag = np.concatenate([a.ravel() for a in ctx.get_factors()])
+        assert rel_err(Ag, A) <= 1e-5, (t, rel_err(Ag, A))
+        A = Ag.astype(np.float64)  # continue both from the GPU state
+    ctx.close()
+
+
+def test_fit_reduces_objective(env):
+    gcp, torch = env
+    w = synth.workload_small_gaussian()
+    ctx = gcp.gcp_create(w["dims"], w["coords"], w["vals"], 4, "gaussian", seed=8)
+    ctx.set_factors(w["factors"])
+    rep = ctx.fit(gcp.AdamParams(lr=1e-2), 1000, 1000, 5000, 5000, iters=100, max_epochs=20)
+    assert rep["objective"] < 0.5 * rep["objective0"]
+    assert rep["epochs"] >= 1 and rep["iterations"] >= 100
+    assert 1.0 <= rep["attempts_per_zero"] < 1.2
+    ctx.close()
+
+
+# ----------------------------------------------------------- edge cases
+def test_empty_sample_sets(env):
+    gcp, torch = env
+    w = synth.workload_small_gaussian()
+    ctx = gcp.gcp_create(w["dims"], w["coords"], w["vals"], 4, "gaussian", seed=1)
+    ctx.set_factors(w["factors"])
+    L, G = gpu_grad(gcp, torch, ctx, 0, 0, 0)
+    assert L == 0.0 and not np.any(G)
+    L, G = gpu_grad(gcp, torch, ctx, 0, 37, 0)  # nonzeros only
+    idx, x, wt, _ = oracle.stratified_samples(1, 0, 37, 0, w["dims"], w["coords"], w["vals"])
+    Lo, Go = oracle.sampled_loss_grad(w["dims"], w["factors"], "gaussian", idx, x, wt)
+    assert abs(L - Lo) <= TOL_FP32 * abs(Lo)
+    ctx.close()
+
+
+def test_exhausted_zero_draw_is_reported(env):
+    gcp, torch = env
+    dims = [3, 2, 2]
+    coords = np.array(list(np.ndindex(*dims)), dtype=np.int32)
+    ctx = gcp.gcp_create(dims, coords, np.ones(len(coords), np.float32), 2, "poisson", max_attempts=8)
+    with pytest.raises(gcp.GcpError) as e:
+        ctx.loss_value(0, 4, 4)
+    assert e.value.status == "ERR_SAMPLER_EXHAUSTED"
+    assert ctx.loss_value(0, 4, 0) == ctx.loss_value(0, 4, 0)  # context still usable
+    ctx.close()
+
+
+def test_duplicate_nonzeros_rejected(env):
+    gcp, torch = env
+    coords = np.array([[0, 1, 1], [2, 0, 1], [0, 1, 1]], dtype=np.int32)
+    with pytest.raises(gcp.GcpError) as e:
+        gcp.gcp_create([3, 2, 2], coords, np.ones(3, np.float32), 2, "poisson")
+    assert e.value.status == "ERR_DUPLICATE"
+
+
+# ------------------------------------------------------------ full size
+@pytest.fixture(scope="module")
+def zipf_full():
+    return synth.cached("zipf_count_full", lambda: synth.workload_zipf_count(scale=1.0))
+
+
+@pytest.mark.parametrize("dtype,tol", [("fp32", TOL_FP32), ("bf16", 1e-5)])
+def test_zipf_count_full_size(env, zipf_full, dtype, tol):
+    """2000x1500x1000x200, 5e7 Zipf nonzeros, rank 32, Poisson, 2^20 + 2^20
+    samples: every sampled index, the loss and all four gradients against
+    the oracle, in the launch configuration the benchmark times."""
+    gcp, torch = env
+    w = zipf_full
+    ctx = gcp.gcp_create(w["dims"], w["coords"], w["vals"], 32, "poisson", dtype=dtype, seed=3002)
+    ctx.set_factors(w["factors"])
+    skeys = oracle.sorted_keys(w["dims"], w["coords"])
+    idx, x, wt, att = oracle.stratified_samples(3002, 5, w["p"], w["q"], w["dims"], w["coords"], w["vals"],
+                                                skeys=skeys)
+    gidx, gx, _ = ctx.sample(5, w["p"], w["q"])
+    assert np.array_equal(gidx.cpu().numpy(), idx)
+    assert np.array_equal(gx.cpu().numpy(), x.astype(np.float32))
+    Lg, Gg = gpu_grad(gcp, torch, ctx, 5, w["p"], w["q"])
+    fac = [bf16_round(a) for a in w["factors"]] if dtype == "bf16" else w["factors"]
+    Lo, Go = oracle.sampled_loss_grad(w["dims"], fac, "poisson", idx, x, wt)
+    assert abs(Lg - Lo) <= tol * abs(Lo), (Lg, Lo)
+    for n, (a, b) in enumerate(zip(split(Gg, w["dims"], 32), Go)):
+        assert rel_err(a, b) <= tol, (dtype, n, rel_err(a, b))
+    if dtype == "bf16":
+        Lf, Gf = oracle.sampled_loss_grad(w["dims"], w["factors"], "poisson", idx, x, wt)
+        assert abs(Lg - Lf) <= TOL_BF16 * abs(Lf)
+        assert rel_err(Gg, np.concatenate([g.ravel() for g in Gf])) <= TOL_BF16
+    ctx.close()
