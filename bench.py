@@ -39,9 +39,11 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def workload():
+def workload(nnz=None):
     import synth
 
+    if nnz:
+        return synth.cached(f"zipf_count_nnz{int(nnz)}", lambda: synth.workload_zipf_count(nnz=nnz))
     return synth.cached("zipf_count_full", lambda: synth.workload_zipf_count(scale=1.0))
 
 
@@ -212,11 +214,11 @@ def run_ours(args):
         dist.barrier()
     gcp.load()
     if rank == 0:
-        w = workload()
+        w = workload(args.nnz)
     if dist:
         dist.barrier()
     if rank != 0:
-        w = workload()
+        w = workload(args.nnz)
     dims, R, p, q = w["dims"], w["rank"], w["p"], w["q"]
     S = p + q
     stream = torch.cuda.current_stream()
@@ -255,6 +257,12 @@ def run_ours(args):
         ctx.profile(False)
         return ms, kms, nl
 
+    if args.kernel_only:  # profiling captures: the timed loop of one variant only
+        ctx = make(args.dtype)
+        ms, kernel_ms, launches = timed_loop(ctx, args.steps, args.warmup, profile=True)
+        log(f"kernel-only {args.dtype}: {kernel_ms / max(1, launches):.4f} ms per fused launch")
+        ctx.close()
+        return
     ctx = make("fp32")
     with ClockSampler(local) as clk:
         ms, kernel_ms, launches = timed_loop(ctx, args.steps, args.warmup, profile=True)
@@ -336,6 +344,10 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nnz", type=float, default=None,
+                    help="nonzero count of a smaller tensor of the same shape (profiling captures)")
+    ap.add_argument("--kernel-only", action="store_true", help="time the step loop only (profiling)")
+    ap.add_argument("--dtype", default="fp32", choices=["fp32", "bf16"], help="factor storage for --kernel-only")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -96,6 +97,9 @@ void destroy_buffers(gcp_ctx *c) {
     cudaFree(c->dloss);
     cudaFree(c->status);
     cudaFree(c->det_scratch);
+    cudaFree(c->hot_slot);
+    cudaFree(c->hot_row);
+    cudaFree(c->Grep);
     cudaFree(c->bk_A);
     cudaFree(c->bk_B);
     cudaFree(c->bk_C);
@@ -162,14 +166,15 @@ gcp_status init_common(gcp_ctx *c, int32_t ndim, const int64_t *dims, int32_t ra
         c->rowoff[k] = c->total_rows;
         c->total_rows += dims[k];
     }
-    const int vec = c->opt.factor_dtype == GCP_BF16 ? 8 : 4;
-    int L = 1, log2L = 0;
-    while (L * vec < rank) {
+    int L = 1, log2L = 0;  // lanes per sample; each lane owns 8 columns
+    while (L * 8 < rank) {
         L <<= 1;
         ++log2L;
     }
-    c->Rp = L * vec;
+    c->Rp = L * 8;
     c->log2L = log2L;
+    if ((double)c->total_rows * c->Rp >= 2147483647.0)
+        return fail(nullptr, GCP_ERR_ARG, "sum of mode sizes x padded rank must be < 2^31");
 
     const size_t nparam = (size_t)c->total_rows * c->Rp;
     cudaError_t e;
@@ -249,12 +254,15 @@ gcp_status run_fused(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad,
     f.G = grad ? c->G : nullptr;
     f.Rp = c->Rp;
     f.log2L = c->log2L;
-    for (int k = 0; k < c->d; ++k) f.rowoff[k] = c->rowoff[k];
+    for (int k = 0; k < c->d; ++k) f.rowoff[k] = (int)c->rowoff[k];
     f.loss = c->loss;
     f.w_nz = (float)w_nz;
     f.w_z = (float)w_z;
     f.dscale = dscale;
     f.partials = c->partials;
+    f.hot_slot = c->hot_slot;
+    f.Grep = c->Grep;
+    f.Htot = c->Htot;
     if (grad) GCP_CUDA(c, cudaMemsetAsync(c->G, 0, (size_t)c->total_rows * c->Rp * 4, c->st));
     int blocks = 0;
     cudaEvent_t stop = nullptr;
@@ -266,6 +274,8 @@ gcp_status run_fused(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad,
         GCP_CUDA(c, gcpk::launch_fused(f, c->Abf != nullptr, c->max_blocks, c->st, &blocks));
     }
     if (stop) GCP_CUDA(c, cudaEventRecord(stop, c->st));
+    if (grad && c->opt.mttkrp == GCP_MTTKRP_ATOMIC)
+        GCP_CUDA(c, gcpk::launch_fold_replicas(c->G, c->Grep, c->hot_row, c->Htot, c->Rp, c->st));
     GCP_CUDA(c, gcpk::launch_finish_loss(c->partials, blocks, w_nz, w_z, c->dloss, c->status, c->st));
     return GCP_OK;
 }
@@ -287,6 +297,40 @@ gcp_status read_loss(gcp_ctx *c, double *loss_out) {
 gcp_status refresh_bf16(gcp_ctx *c) {
     if (!c->Abf) return GCP_OK;
     GCP_CUDA(c, gcpk::launch_to_bf16((int64_t)c->total_rows * c->Rp, c->A, c->Abf, c->st));
+    return GCP_OK;
+}
+
+// Rows that receive many gradient reductions per call get replicas: rows
+// holding at least 1/512 of the nonzeros (hit by that share of the nonzero
+// samples) and every row of a mode with at most 512 rows (hit by 1/I_k of
+// the zero or uniform samples); at most 4096 rows, hottest first.
+gcp_status setup_hot_rows(gcp_ctx *c, const std::vector<int64_t> &counts) {
+    std::vector<std::pair<double, int>> cand;
+    for (int k = 0; k < c->d; ++k) {
+        const double uni = 1.0 / (double)c->dims[k];
+        for (int64_t i = 0; i < c->dims[k]; ++i) {
+            const int row = (int)(c->rowoff[k] + i);
+            const double nz = counts.empty() ? 0.0 : (double)counts[row] / (double)c->nnz;
+            if (nz * 512.0 >= 1.0 || c->dims[k] <= 512) cand.push_back({nz > uni ? nz : uni, row});
+        }
+    }
+    std::stable_sort(cand.begin(), cand.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
+    if (cand.size() > 4096) cand.resize(4096);
+    c->Htot = (int)cand.size();
+    if (c->Htot == 0) return GCP_OK;
+    std::vector<int> slot((size_t)c->total_rows, -1), row(cand.size());
+    for (size_t s = 0; s < cand.size(); ++s) {
+        slot[cand[s].second] = (int)s;
+        row[s] = cand[s].second;
+    }
+    const size_t rep_bytes = (size_t)gcpk::kReplicas * c->Htot * c->Rp * 4;
+    cudaError_t e;
+    if ((e = cudaMalloc(&c->hot_slot, slot.size() * 4)) || (e = cudaMalloc(&c->hot_row, row.size() * 4)) ||
+        (e = cudaMalloc(&c->Grep, rep_bytes)) ||
+        (e = cudaMemcpy(c->hot_slot, slot.data(), slot.size() * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->hot_row, row.data(), row.size() * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemsetAsync(c->Grep, 0, rep_bytes, c->st)))
+        return cuda_fail(nullptr, e, "allocating hot-row replicas");
     return GCP_OK;
 }
 
@@ -340,6 +384,17 @@ gcp_status gcp_create(int32_t ndim, const int64_t *dims, int64_t nnz, const int3
         return fail(nullptr, GCP_ERR_ARG, "more nonzeros than cells");
     }
     c->nnz = nnz;
+    {
+        std::vector<int64_t> counts((size_t)c->total_rows, 0);
+        for (int64_t e = 0; e < nnz; ++e)
+            for (int k = 0; k < ndim; ++k) ++counts[(size_t)(c->rowoff[k] + coords[e * ndim + k])];
+        s = setup_hot_rows(c, counts);
+        if (s) {
+            destroy_buffers(c);
+            delete c;
+            return s;
+        }
+    }
     c->rec_words = gcpk::rec_words_for(ndim);
     const uint64_t cap = next_pow2((uint64_t)std::ceil((double)nnz / c->opt.hash_max_load)) < 4
                              ? 4
@@ -400,6 +455,12 @@ gcp_status gcp_create_dense(int32_t ndim, const int64_t *dims, const float *X, i
     }
     c->dense = true;
     c->nnz = (int64_t)c->M;
+    s = setup_hot_rows(c, std::vector<int64_t>());
+    if (s) {
+        destroy_buffers(c);
+        delete c;
+        return s;
+    }
     const size_t bytes = (size_t)c->M * 4;
     cudaError_t e;
     if ((e = cudaMalloc(&c->X, bytes)) ||

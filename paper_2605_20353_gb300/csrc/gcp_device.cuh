@@ -67,11 +67,11 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {  // splitmix64 finalizer
     return x;
 }
 
+// Lookup continuing at bucket b after `done` buckets were searched:
 // 1 = present, 0 = absent, -1 = probed every bucket without an answer.
-__device__ __forceinline__ int hash_contains(const uint64_t *__restrict__ keys, uint64_t bmask,
-                                             uint64_t key) {
-    uint64_t b = mix64(key) & bmask;
-    for (uint64_t probe = 0; probe <= bmask; ++probe) {
+__device__ __forceinline__ int hash_contains_from(const uint64_t *__restrict__ keys, uint64_t bmask,
+                                                  uint64_t key, uint64_t b, uint64_t done) {
+    for (uint64_t probe = done; probe <= bmask; ++probe) {
         const ulonglong2 *slot = reinterpret_cast<const ulonglong2 *>(keys + 4 * b);
         const ulonglong2 lo = __ldg(slot), hi = __ldg(slot + 1);
         if (lo.x == key || lo.y == key || hi.x == key || hi.y == key) return 1;
@@ -79,6 +79,18 @@ __device__ __forceinline__ int hash_contains(const uint64_t *__restrict__ keys, 
         b = (b + 1) & bmask;
     }
     return -1;
+}
+
+__device__ __forceinline__ int hash_contains(const uint64_t *__restrict__ keys, uint64_t bmask, uint64_t key) {
+    return hash_contains_from(keys, bmask, key, mix64(key) & bmask, 0);
+}
+
+// Decide a lookup from one bucket already in registers: 1 / 0 as above,
+// 2 = bucket full without the key (continue at the next bucket).
+__device__ __forceinline__ int bucket_decide(ulonglong2 lo, ulonglong2 hi, uint64_t key) {
+    if (lo.x == key || lo.y == key || hi.x == key || hi.y == key) return 1;
+    if (lo.x == kEmpty || lo.y == kEmpty || hi.x == kEmpty || hi.y == kEmpty) return 0;
+    return 2;
 }
 
 // 0 = inserted, kErrDuplicate, or kErrHashFull.
@@ -131,13 +143,15 @@ __device__ __forceinline__ void loss_eval(int loss, float x, float m, float &f, 
 }
 
 // ------------------------------------------------------------ vector I/O
+// Four consecutive factor entries widened to FP32 (16 B of FP32 or 8 B of
+// BF16), read through the non-coherent path: factors do not change while a
+// kernel runs.
 template <typename TF>
-struct Vec;  // 16 bytes of factor entries widened to FP32
+struct Quad;
 
 template <>
-struct Vec<float> {
-    static constexpr int N = 4;
-    __device__ __forceinline__ static void load(const float *p, float (&o)[4]) {
+struct Quad<float> {
+    __device__ __forceinline__ static void load(const float *p, float *o) {
         const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
         o[0] = v.x;
         o[1] = v.y;
@@ -147,18 +161,30 @@ struct Vec<float> {
 };
 
 template <>
-struct Vec<__nv_bfloat16> {
-    static constexpr int N = 8;
-    __device__ __forceinline__ static void load(const __nv_bfloat16 *p, float (&o)[8]) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            o[2 * i] = __uint_as_float(w[i] << 16);
-            o[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
-        }
+struct Quad<__nv_bfloat16> {
+    __device__ __forceinline__ static void load(const __nv_bfloat16 *p, float *o) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+        o[0] = __uint_as_float(v.x << 16);
+        o[1] = __uint_as_float(v.x & 0xFFFF0000u);
+        o[2] = __uint_as_float(v.y << 16);
+        o[3] = __uint_as_float(v.y & 0xFFFF0000u);
     }
 };
+
+// Asynchronous global -> shared copies (LDGSTS), grouped per thread.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Fire-and-forget FP32 vector reduction into global memory (sm_90+).
 __device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d) {

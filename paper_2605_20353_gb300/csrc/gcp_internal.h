@@ -36,14 +36,21 @@ struct FusedSpec {
     SampleSpec s;
     const void *F;                  // factors the kernels read (FP32 or BF16), row stride Rp
     float *G;                       // gradient, row stride Rp; null = loss only
-    int Rp;                         // padded row length (elements)
-    int log2L;                      // lanes per sample = Rp / (16 B / element size)
-    int64_t rowoff[GCP_MAX_NDIM];   // first row of each mode in F and G
+    int Rp;                         // padded row length: 8 x lanes per sample (power of 2)
+    int log2L;                      // log2(lanes per sample); each lane owns 8 columns
+    int rowoff[GCP_MAX_NDIM];       // first row of each mode in F and G
     int loss;
     float w_nz, w_z;                // per-sample weights (FP32 copies)
     const float *dscale;            // gradient scale (device) or null
     double *partials;               // per block: sum f over nonzero / zero samples, attempts, -
+    const int *hot_slot;            // row -> replica slot, -1 = not replicated (null = none)
+    float *Grep;                    // kReplicas x Htot x Rp replica rows (zero between calls)
+    int Htot;                       // replicated rows
 };
+
+// Rows that many samples hit (Zipf heads, rows of small modes) are
+// accumulated in this many global replicas, then folded into G.
+constexpr int kReplicas = 32;
 
 struct LaunchCfg {
     int blocks;
@@ -58,6 +65,7 @@ cudaError_t launch_build_records(const int32_t *coords, const float *vals, int64
 cudaError_t launch_sample(const SampleSpec &s, int32_t *idx_out, float *x_out, float *w_out, float w_nz,
                           float w_z, cudaStream_t st);
 cudaError_t launch_fused(const FusedSpec &f, bool bf16, int max_blocks, cudaStream_t st, int *blocks_used);
+cudaError_t launch_fold_replicas(float *G, float *Grep, const int *hot_row, int Htot, int Rp, cudaStream_t st);
 cudaError_t launch_finish_loss(const double *partials, int nblocks, double w_nz, double w_z, double *dloss,
                                int *status, cudaStream_t st);
 cudaError_t launch_adam(int64_t n, int Rp, int R, float *A, float *B, float *C, const float *G, float lr,
@@ -100,6 +108,12 @@ struct gcp_ctx {
     int *status = nullptr;        // device status word
     int *h_status = nullptr;      // pinned mirror
     double *h_loss = nullptr;     // pinned mirror of dloss
+
+    // hot-row replicas of the gradient
+    int *hot_slot = nullptr;      // [total_rows]
+    int *hot_row = nullptr;       // [Htot]
+    float *Grep = nullptr;        // [kReplicas x Htot x Rp]
+    int Htot = 0;
 
     // deterministic MTTKRP scratch
     void *det_scratch = nullptr;

@@ -103,16 +103,35 @@ __device__ __forceinline__ bool draw_sample(const SampleSpec &S, int64_t s, int3
 }
 
 // ------------------------------------------------------------ fused pass
+// Per warp and per tile of 32 consecutive samples:
+//   A1 (tile t+1, one sample per lane): Philox draw; the nonzero record, the
+//      dense value or the first hash bucket of the zero candidate is copied
+//      into shared memory with cp.async while tile t is processed;
+//   A2 (tile t): finish the draw -- a zero candidate found in its bucket is
+//      rejected and redrawn with direct probes (rare: 1/(1-N/M) attempts);
+//   B  (tile t, one sample per group of L = Rp/8 lanes): lane g owns columns
+//      4g..4g+3 and Rp/2+4g..Rp/2+4g+3, so every load and reduction of a
+//      group covers whole 32-byte sectors.
+// Gradient rows that many samples hit go to one of kReplicas replicas
+// (chosen by warp), folded into G afterwards, so that the reductions of hot
+// rows do not serialise on one address.
+constexpr int kWarps = kThreads / 32;
+
 template <int D, typename TF>
-__global__ void __launch_bounds__(kThreads) k_fused(const FusedSpec P) {
-    constexpr int VEC = Vec<TF>::N;
+__global__ void __launch_bounds__(kThreads, (D <= 4 ? 3 : 1)) k_fused(const FusedSpec P) {
+    constexpr int SW = rec_words_for(D);  // words per staged sample: coordinates, value, padding
+    __shared__ __align__(16) int32_t s_slot[2][kWarps][32][SW];
+    __shared__ __align__(16) uint64_t s_bkt[2][kWarps][32][4];
+
     const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     const int log2L = P.log2L;
     const int L = 1 << log2L;
     const int glane = lane & (L - 1);
     const int grp = lane >> log2L;
     const int ngrp = 32 >> log2L;
     const unsigned gmask = (L == 32) ? 0xFFFFFFFFu : (((1u << L) - 1u) << (grp * L));
+    const int c0 = 4 * glane, c1 = (P.Rp >> 1) + 4 * glane;
     const int64_t S = P.s.p + P.s.q;
     const int64_t ntiles = (S + 31) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -120,44 +139,125 @@ __global__ void __launch_bounds__(kThreads) k_fused(const FusedSpec P) {
     const TF *__restrict__ F = static_cast<const TF *>(P.F);
     const float scale = P.dscale ? __ldg(P.dscale) : 1.0f;
     const bool semi = P.s.sampling == GCP_SAMPLING_SEMI_STRATIFIED;
+    const bool uniform = P.s.sampling == GCP_SAMPLING_UNIFORM;
+    float *const grep = P.Grep ? P.Grep + (size_t)(warp0 & (kReplicas - 1)) * P.Htot * P.Rp : nullptr;
 
     double acc_nz = 0.0, acc_z = 0.0;
     int attempts = 0;
 
-    for (int64_t tile = warp0; tile < ntiles; tile += nwarps) {
-        // phase A: one sample per lane
-        const int64_t s_mine = (tile << 5) + lane;
-        int32_t idx[D] = {};
-        float x = 0.0f;
-        bool ok = false;
-        if (s_mine < S) ok = draw_sample<D>(P.s, s_mine, idx, x, attempts);
+    // A1: start the draw of sample s into stage `st`; returns the key of a
+    // stratified zero candidate (kEmpty otherwise).
+    auto issue = [&](int64_t tile, int st) -> uint64_t {
+        const int64_t s = (tile << 5) + lane;
+        int32_t *slot = s_slot[st][warp][lane];
+        if (tile >= ntiles || s >= S) return kEmpty;
+        if (uniform) {
+            int32_t idx[D];
+            draw_tuple<D>(P.s, kStreamUniform, (uint64_t)s, 0, idx);
+#pragma unroll
+            for (int k = 0; k < D; ++k) slot[k] = idx[k];
+            cp_async4(slot + D, P.s.dense + linear_of<D>(P.s, idx));
+            return kEmpty;
+        }
+        if (s < P.s.p) {
+            const U64x4 w = philox4x64_10((uint64_t)s, 0, P.s.iter, 0, P.s.seed, kStreamNonzero);
+            const int32_t *rec = P.s.rec + map_range(w.v[0], (uint64_t)P.s.nnz) * SW;
+#pragma unroll
+            for (int v = 0; v < SW / 4; ++v) cp_async16(slot + 4 * v, rec + 4 * v);
+            return kEmpty;
+        }
+        int32_t idx[D];
+        draw_tuple<D>(P.s, semi ? kStreamSemiZero : kStreamZero, (uint64_t)(s - P.s.p), 0, idx);
+#pragma unroll
+        for (int k = 0; k < D; ++k) slot[k] = idx[k];
+        slot[D] = 0;  // x = 0.0f
+        if (semi) return kEmpty;
+        const uint64_t key = linear_of<D>(P.s, idx);
+        const uint64_t *b = P.s.hkeys + 4 * (mix64(key) & P.s.hbmask);
+        cp_async16(&s_bkt[st][warp][lane][0], b);
+        cp_async16(&s_bkt[st][warp][lane][2], b + 2);
+        return key;
+    };
 
-        // phase B: one sample per group of L lanes
+    // A2: finish the draw of stage `st`; returns whether the sample exists.
+    auto finish = [&](int64_t tile, int st, uint64_t key) -> bool {
+        const int64_t s = (tile << 5) + lane;
+        if (s >= S) return false;
+        if (key == kEmpty) return true;  // nonzero, semi-stratified or dense draw
+        const ulonglong2 lo = *reinterpret_cast<const ulonglong2 *>(&s_bkt[st][warp][lane][0]);
+        const ulonglong2 hi = *reinterpret_cast<const ulonglong2 *>(&s_bkt[st][warp][lane][2]);
+        int h = bucket_decide(lo, hi, key);
+        if (h == 2)
+            h = hash_contains_from(P.s.hkeys, P.s.hbmask, key, ((mix64(key) & P.s.hbmask) + 1) & P.s.hbmask, 1);
+        if (h == 0) {
+            attempts += 1;
+            return true;
+        }
+        // rejected: redraw until a candidate is absent (Sec. 3.1.1)
+        int32_t *slot = s_slot[st][warp][lane];
+        const uint64_t j = (uint64_t)(s - P.s.p);
+        for (int a = 1; h == 1 && a < P.s.max_attempts; ++a) {
+            int32_t idx[D];
+            draw_tuple<D>(P.s, kStreamZero, j, 4 * (uint64_t)a, idx);
+            h = hash_contains(P.s.hkeys, P.s.hbmask, linear_of<D>(P.s, idx));
+            if (h == 0) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) slot[k] = idx[k];
+                attempts += a + 1;
+                return true;
+            }
+        }
+        if (h < 0) {
+            atomicOr(P.s.status, kErrHashFull);
+        } else {
+            attempts += P.s.max_attempts;
+            atomicOr(P.s.status, kErrExhausted);
+        }
+        return false;
+    };
+
+    int64_t tile = warp0;
+    uint64_t key_next = issue(tile, 0);
+    cp_async_commit();
+    for (int st = 0; tile < ntiles; tile += nwarps, st ^= 1) {
+        const uint64_t key = key_next;
+        __syncwarp();  // stage st^1 is free: the previous tile's phase B is done
+        key_next = issue(tile + nwarps, st ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();  // this lane's copies into stage st have landed
+        const bool ok = finish(tile, st, key);
+        const unsigned okmask = __ballot_sync(0xFFFFFFFFu, ok);
+        __syncwarp();  // every lane's staged sample is visible to the warp
+
+        // phase B: one sample per group
         for (int it = 0; it < L; ++it) {
             const int src = it * ngrp + grp;
+            if (!((okmask >> src) & 1u)) continue;  // uniform within the group
+            const int32_t *slot = s_slot[st][warp][src];
             int32_t ii[D];
 #pragma unroll
-            for (int k = 0; k < D; ++k) ii[k] = __shfl_sync(0xFFFFFFFFu, idx[k], src);
-            const float xs = __shfl_sync(0xFFFFFFFFu, x, src);
-            const int oks = __shfl_sync(0xFFFFFFFFu, (int)ok, src);
-            if (!oks) continue;  // uniform within the group
+            for (int k = 0; k < D; ++k) ii[k] = slot[k];
+            const float xs = __int_as_float(slot[D]);
             const bool is_nz = ((tile << 5) + src) < P.s.p;
 
-            float a[D][VEC];
+            int off[D];
+            float a[D][8];
 #pragma unroll
-            for (int k = 0; k < D; ++k)
-                Vec<TF>::load(F + (P.rowoff[k] + ii[k]) * (int64_t)P.Rp + glane * VEC, a[k]);
-            // suffix products suf[k] = prod_{j>k} a_j
-            float suf[D][VEC];
+            for (int k = 0; k < D; ++k) {
+                off[k] = (P.rowoff[k] + ii[k]) * P.Rp;
+                Quad<TF>::load(F + off[k] + c0, a[k]);
+                Quad<TF>::load(F + off[k] + c1, a[k] + 4);
+            }
+            float suf[D][8];  // suf[k] = prod_{j>k} a_j
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) suf[D - 1][v] = 1.0f;
+            for (int v = 0; v < 8; ++v) suf[D - 1][v] = 1.0f;
 #pragma unroll
             for (int k = D - 2; k >= 0; --k)
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) suf[k][v] = suf[k + 1][v] * a[k + 1][v];
+                for (int v = 0; v < 8; ++v) suf[k][v] = suf[k + 1][v] * a[k + 1][v];
             float m = 0.0f;
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) m += a[0][v] * suf[0][v];
+            for (int v = 0; v < 8; ++v) m = fmaf(a[0][v], suf[0][v], m);
             for (int o = L >> 1; o > 0; o >>= 1) m += __shfl_xor_sync(gmask, m, o);
 
             float f, df;
@@ -176,22 +276,24 @@ __global__ void __launch_bounds__(kThreads) k_fused(const FusedSpec P) {
             }
             if (P.G) {
                 const float y = (is_nz ? P.w_nz : P.w_z) * df * scale;
-                float pre[VEC];
+                float pre[8];
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) pre[v] = y;
+                for (int v = 0; v < 8; ++v) pre[v] = y;
 #pragma unroll
                 for (int n = 0; n < D; ++n) {
-                    float *g = P.G + (P.rowoff[n] + ii[n]) * (int64_t)P.Rp + glane * VEC;
+                    const int hs = P.hot_slot ? __ldg(P.hot_slot + P.rowoff[n] + ii[n]) : -1;
+                    float *g = hs >= 0 ? grep + hs * P.Rp : P.G + off[n];
+                    red_add_v4(g + c0, pre[0] * suf[n][0], pre[1] * suf[n][1], pre[2] * suf[n][2],
+                               pre[3] * suf[n][3]);
+                    red_add_v4(g + c1, pre[4] * suf[n][4], pre[5] * suf[n][5], pre[6] * suf[n][6],
+                               pre[7] * suf[n][7]);
 #pragma unroll
-                    for (int h = 0; h < VEC; h += 4)
-                        red_add_v4(g + h, pre[h] * suf[n][h], pre[h + 1] * suf[n][h + 1],
-                                   pre[h + 2] * suf[n][h + 2], pre[h + 3] * suf[n][h + 3]);
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) pre[v] *= a[n][v];
+                    for (int v = 0; v < 8; ++v) pre[v] *= a[n][v];
                 }
             }
         }
     }
+    cp_async_wait<0>();
 
     // block reduction of the FP64 loss sums and attempt counts
     double att = (double)attempts;
@@ -201,8 +303,8 @@ __global__ void __launch_bounds__(kThreads) k_fused(const FusedSpec P) {
         acc_z += __shfl_xor_sync(0xFFFFFFFFu, acc_z, o);
         att += __shfl_xor_sync(0xFFFFFFFFu, att, o);
     }
-    __shared__ double red[3][kThreads / 32];
-    const int warp = threadIdx.x >> 5;
+    double(*red)[kWarps] = reinterpret_cast<double(*)[kWarps]>(&s_bkt[0][0][0][0]);  // staging is free now
+    __syncthreads();
     if (lane == 0) {
         red[0][warp] = acc_nz;
         red[1][warp] = acc_z;
@@ -211,8 +313,26 @@ __global__ void __launch_bounds__(kThreads) k_fused(const FusedSpec P) {
     __syncthreads();
     if (threadIdx.x < 3) {
         double t = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) t += red[threadIdx.x][w];
+        for (int w = 0; w < kWarps; ++w) t += red[threadIdx.x][w];
         P.partials[4 * blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+// G(hot row) = sum over replicas, then the replicas are cleared for the
+// next call (fixed replica order).
+__global__ void k_fold_replicas(float *__restrict__ G, float *__restrict__ Grep, const int *__restrict__ hot_row,
+                                int Htot, int Rp) {
+    const int64_t n = (int64_t)Htot * Rp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int slot = (int)(e / Rp), col = (int)(e % Rp);
+        float t = 0.0f;
+#pragma unroll 8
+        for (int r = 0; r < kReplicas; ++r) {
+            float *p = Grep + ((int64_t)r * Htot + slot) * Rp + col;
+            t += *p;
+            *p = 0.0f;
+        }
+        G[(int64_t)hot_row[slot] * Rp + col] = t;
     }
 }
 
@@ -393,6 +513,12 @@ cudaError_t launch_fused(const FusedSpec &f, bool bf16, int max_blocks, cudaStre
         k_fused<D, float><<<blocks, kThreads, 0, st>>>(f)
     GCP_DISPATCH_D(f.s.d, GCP_LAUNCH_FUSED)
 #undef GCP_LAUNCH_FUSED
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_replicas(float *G, float *Grep, const int *hot_row, int Htot, int Rp, cudaStream_t st) {
+    if (Htot == 0) return cudaSuccess;
+    k_fold_replicas<<<elementwise_blocks((int64_t)Htot * Rp), kThreads, 0, st>>>(G, Grep, hot_row, Htot, Rp);
     return cudaGetLastError();
 }
 

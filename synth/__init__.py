@@ -211,12 +211,13 @@ def workload_small_gaussian(seed=1001):
                 factors=factors_uniform(dims, 4, seed + 1000), p=1000, q=1000)
 
 
-def workload_zipf_count(scale=1.0, seed=1002):
+def workload_zipf_count(scale=1.0, seed=1002, nnz=None):
     """2000 x 1500 x 1000 x 200 Zipf(1.1) count tensor with 5e7 nonzeros,
     Poisson loss, rank 32, 2^20 + 2^20 samples.  `scale` < 1 shrinks the
-    nonzero count and samples proportionally for quick tests."""
+    nonzero count and samples proportionally for quick tests; `nnz` sets
+    the nonzero count alone (full sample counts), for profiling captures."""
     dims = [2000, 1500, 1000, 200]
-    nnz = max(1000, int(5e7 * scale))
+    nnz = int(nnz) if nnz else max(1000, int(5e7 * scale))
     coords, vals = zipf_sparse(dims, nnz, seed, s=1.1, lam=3.0)
     S = max(256, int((1 << 20) * scale))
     return dict(dims=dims, coords=coords, vals=vals, rank=32, loss="poisson",
