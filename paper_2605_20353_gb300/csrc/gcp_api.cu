@@ -166,12 +166,15 @@ gcp_status init_common(gcp_ctx *c, int32_t ndim, const int64_t *dims, int32_t ra
         c->rowoff[k] = c->total_rows;
         c->total_rows += dims[k];
     }
-    int L = 1, log2L = 0;  // lanes per sample; each lane owns 8 columns
-    while (L * 8 < rank) {
-        L <<= 1;
-        ++log2L;
-    }
-    c->Rp = L * 8;
+    // Row length padded to 4 x a power of two.  A lane owns 4 columns when a
+    // row is at most 32 floats (a group's reduction covers the whole
+    // 128-byte row), else 8 (two half rows of >= 128 bytes).
+    int Rp = 4;
+    while (Rp < rank) Rp <<= 1;
+    c->Rp = Rp;
+    c->cols = Rp >= 64 ? 8 : 4;
+    int L = Rp / c->cols, log2L = 0;
+    while ((1 << log2L) < L) ++log2L;
     c->log2L = log2L;
     if ((double)c->total_rows * c->Rp >= 2147483647.0)
         return fail(nullptr, GCP_ERR_ARG, "sum of mode sizes x padded rank must be < 2^31");
@@ -185,7 +188,7 @@ gcp_status init_common(gcp_ctx *c, int32_t ndim, const int64_t *dims, int32_t ra
         return cuda_fail(nullptr, e, "allocating model buffers");
     if (c->opt.factor_dtype == GCP_BF16 && (e = cudaMalloc(&c->Abf, nparam * 2)))
         return cuda_fail(nullptr, e, "allocating BF16 factors");
-    c->max_blocks = gcpk::fused_max_blocks(ndim, c->opt.factor_dtype == GCP_BF16);
+    c->max_blocks = gcpk::fused_max_blocks(ndim, c->opt.factor_dtype == GCP_BF16, c->cols);
     if ((e = cudaMalloc(&c->partials, (size_t)c->max_blocks * 4 * sizeof(double))))
         return cuda_fail(nullptr, e, "allocating partials");
     if ((e = cudaMemsetAsync(c->A, 0, nparam * 4, c->st)) || (e = cudaMemsetAsync(c->G, 0, nparam * 4, c->st)) ||
@@ -271,7 +274,7 @@ gcp_status run_fused(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad,
         s = gcpk_det_grad(c, f, &blocks);
         if (s) return s;
     } else {
-        GCP_CUDA(c, gcpk::launch_fused(f, c->Abf != nullptr, c->max_blocks, c->st, &blocks));
+        GCP_CUDA(c, gcpk::launch_fused(f, c->Abf != nullptr, c->cols, c->max_blocks, c->st, &blocks));
     }
     if (stop) GCP_CUDA(c, cudaEventRecord(stop, c->st));
     if (grad && c->opt.mttkrp == GCP_MTTKRP_ATOMIC)

@@ -36,8 +36,8 @@ struct FusedSpec {
     SampleSpec s;
     const void *F;                  // factors the kernels read (FP32 or BF16), row stride Rp
     float *G;                       // gradient, row stride Rp; null = loss only
-    int Rp;                         // padded row length: 8 x lanes per sample (power of 2)
-    int log2L;                      // log2(lanes per sample); each lane owns 8 columns
+    int Rp;                         // padded row length: cols x lanes per sample (power of 2)
+    int log2L;                      // log2(lanes per sample); each lane owns cols = 4 or 8 columns
     int rowoff[GCP_MAX_NDIM];       // first row of each mode in F and G
     int loss;
     float w_nz, w_z;                // per-sample weights (FP32 copies)
@@ -64,7 +64,8 @@ cudaError_t launch_build_records(const int32_t *coords, const float *vals, int64
                                  uint64_t hbmask, int *status, cudaStream_t st);
 cudaError_t launch_sample(const SampleSpec &s, int32_t *idx_out, float *x_out, float *w_out, float w_nz,
                           float w_z, cudaStream_t st);
-cudaError_t launch_fused(const FusedSpec &f, bool bf16, int max_blocks, cudaStream_t st, int *blocks_used);
+cudaError_t launch_fused(const FusedSpec &f, bool bf16, int cols, int max_blocks, cudaStream_t st,
+                         int *blocks_used);
 cudaError_t launch_fold_replicas(float *G, float *Grep, const int *hot_row, int Htot, int Rp, cudaStream_t st);
 cudaError_t launch_finish_loss(const double *partials, int nblocks, double w_nz, double w_z, double *dloss,
                                int *status, cudaStream_t st);
@@ -72,7 +73,7 @@ cudaError_t launch_adam(int64_t n, int Rp, int R, float *A, float *B, float *C, 
                         float beta1, float beta2, float c1inv, float c2inv, float eps, float lower,
                         void *Abf, cudaStream_t st);
 cudaError_t launch_to_bf16(int64_t n, const float *A, void *Abf, cudaStream_t st);
-int fused_max_blocks(int d, bool bf16);
+int fused_max_blocks(int d, bool bf16, int cols);
 
 }  // namespace gcpk
 
@@ -83,7 +84,7 @@ struct gcp_ctx {
     uint64_t stride[GCP_MAX_NDIM] = {0};
     int64_t rowoff[GCP_MAX_NDIM] = {0};
     int64_t total_rows = 0;
-    int R = 0, Rp = 0, log2L = 0;
+    int R = 0, Rp = 0, log2L = 0, cols = 4;
     int loss = 0;
     int64_t nnz = 0;
     double M = 0;  // number of cells (exact below 2^53, used for weights)

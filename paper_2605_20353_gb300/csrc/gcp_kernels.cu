@@ -109,17 +109,19 @@ __device__ __forceinline__ bool draw_sample(const SampleSpec &S, int64_t s, int3
 //      into shared memory with cp.async while tile t is processed;
 //   A2 (tile t): finish the draw -- a zero candidate found in its bucket is
 //      rejected and redrawn with direct probes (rare: 1/(1-N/M) attempts);
-//   B  (tile t, one sample per group of L = Rp/8 lanes): lane g owns columns
-//      4g..4g+3 and Rp/2+4g..Rp/2+4g+3, so every load and reduction of a
-//      group covers whole 32-byte sectors.
+//   B  (tile t, one sample per group of L = Rp/COLS lanes): lane g owns
+//      COLS columns as COLS/4 quads (4g..4g+3, and Rp/2+4g.. when COLS = 8),
+//      so a group's loads and vector reductions cover whole 32-byte sectors
+//      and, for rows up to 128 bytes, one whole row per instruction.
 // Gradient rows that many samples hit go to one of kReplicas replicas
 // (chosen by warp), folded into G afterwards, so that the reductions of hot
 // rows do not serialise on one address.
 constexpr int kWarps = kThreads / 32;
 
-template <int D, typename TF>
-__global__ void __launch_bounds__(kThreads, (D <= 4 ? 3 : 1)) k_fused(const FusedSpec P) {
+template <int D, typename TF, int COLS>
+__global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) k_fused(const FusedSpec P) {
     constexpr int SW = rec_words_for(D);  // words per staged sample: coordinates, value, padding
+    constexpr int NQ = COLS / 4;          // quads of columns per lane
     __shared__ __align__(16) int32_t s_slot[2][kWarps][32][SW];
     __shared__ __align__(16) uint64_t s_bkt[2][kWarps][32][4];
 
@@ -131,7 +133,9 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? 3 : 1)) k_fused(const Fuse
     const int grp = lane >> log2L;
     const int ngrp = 32 >> log2L;
     const unsigned gmask = (L == 32) ? 0xFFFFFFFFu : (((1u << L) - 1u) << (grp * L));
-    const int c0 = 4 * glane, c1 = (P.Rp >> 1) + 4 * glane;
+    int col[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) col[q] = q * (P.Rp >> 1) + 4 * glane;
     const int64_t S = P.s.p + P.s.q;
     const int64_t ntiles = (S + 31) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -241,23 +245,23 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? 3 : 1)) k_fused(const Fuse
             const bool is_nz = ((tile << 5) + src) < P.s.p;
 
             int off[D];
-            float a[D][8];
+            float a[D][COLS];
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 off[k] = (P.rowoff[k] + ii[k]) * P.Rp;
-                Quad<TF>::load(F + off[k] + c0, a[k]);
-                Quad<TF>::load(F + off[k] + c1, a[k] + 4);
-            }
-            float suf[D][8];  // suf[k] = prod_{j>k} a_j
 #pragma unroll
-            for (int v = 0; v < 8; ++v) suf[D - 1][v] = 1.0f;
+                for (int q = 0; q < NQ; ++q) Quad<TF>::load(F + off[k] + col[q], a[k] + 4 * q);
+            }
+            float suf[D][COLS];  // suf[k] = prod_{j>k} a_j
+#pragma unroll
+            for (int v = 0; v < COLS; ++v) suf[D - 1][v] = 1.0f;
 #pragma unroll
             for (int k = D - 2; k >= 0; --k)
 #pragma unroll
-                for (int v = 0; v < 8; ++v) suf[k][v] = suf[k + 1][v] * a[k + 1][v];
+                for (int v = 0; v < COLS; ++v) suf[k][v] = suf[k + 1][v] * a[k + 1][v];
             float m = 0.0f;
 #pragma unroll
-            for (int v = 0; v < 8; ++v) m = fmaf(a[0][v], suf[0][v], m);
+            for (int v = 0; v < COLS; ++v) m = fmaf(a[0][v], suf[0][v], m);
             for (int o = L >> 1; o > 0; o >>= 1) m += __shfl_xor_sync(gmask, m, o);
 
             float f, df;
@@ -276,19 +280,19 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? 3 : 1)) k_fused(const Fuse
             }
             if (P.G) {
                 const float y = (is_nz ? P.w_nz : P.w_z) * df * scale;
-                float pre[8];
+                float pre[COLS];
 #pragma unroll
-                for (int v = 0; v < 8; ++v) pre[v] = y;
+                for (int v = 0; v < COLS; ++v) pre[v] = y;
 #pragma unroll
                 for (int n = 0; n < D; ++n) {
                     const int hs = P.hot_slot ? __ldg(P.hot_slot + P.rowoff[n] + ii[n]) : -1;
                     float *g = hs >= 0 ? grep + hs * P.Rp : P.G + off[n];
-                    red_add_v4(g + c0, pre[0] * suf[n][0], pre[1] * suf[n][1], pre[2] * suf[n][2],
-                               pre[3] * suf[n][3]);
-                    red_add_v4(g + c1, pre[4] * suf[n][4], pre[5] * suf[n][5], pre[6] * suf[n][6],
-                               pre[7] * suf[n][7]);
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) pre[v] *= a[n][v];
+                    for (int q = 0; q < NQ; ++q)
+                        red_add_v4(g + col[q], pre[4 * q] * suf[n][4 * q], pre[4 * q + 1] * suf[n][4 * q + 1],
+                                   pre[4 * q + 2] * suf[n][4 * q + 2], pre[4 * q + 3] * suf[n][4 * q + 3]);
+#pragma unroll
+                    for (int v = 0; v < COLS; ++v) pre[v] *= a[n][v];
                 }
             }
         }
@@ -471,48 +475,69 @@ cudaError_t launch_sample(const SampleSpec &s, int32_t *idx_out, float *x_out, f
     return cudaGetLastError();
 }
 
-template <int D, typename TF>
+template <int D, typename TF, int COLS>
 static int occupancy_blocks() {
     static int nb = -1;
     if (nb < 0) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<D, TF>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<D, TF, COLS>, kThreads, 0);
         nb = (per_sm < 1 ? 1 : per_sm) * num_sms();
     }
     return nb;
 }
 
-int fused_max_blocks(int d, bool bf16) {
-    int nb = 0;
-#define GCP_OCC(D) nb = bf16 ? occupancy_blocks<D, __nv_bfloat16>() : occupancy_blocks<D, float>()
-    switch (d) {
-    case 2: GCP_OCC(2); break;
-    case 3: GCP_OCC(3); break;
-    case 4: GCP_OCC(4); break;
-    case 5: GCP_OCC(5); break;
-    case 6: GCP_OCC(6); break;
-    case 7: GCP_OCC(7); break;
-    case 8: GCP_OCC(8); break;
-    default: nb = num_sms();
-    }
-#undef GCP_OCC
-    return nb;
+template <int D>
+static int occupancy_of(bool bf16, int cols) {
+    if (bf16) return cols == 8 ? occupancy_blocks<D, __nv_bfloat16, 8>() : occupancy_blocks<D, __nv_bfloat16, 4>();
+    return cols == 8 ? occupancy_blocks<D, float, 8>() : occupancy_blocks<D, float, 4>();
 }
 
-cudaError_t launch_fused(const FusedSpec &f, bool bf16, int max_blocks, cudaStream_t st, int *blocks_used) {
+int fused_max_blocks(int d, bool bf16, int cols) {
+    switch (d) {
+    case 2: return occupancy_of<2>(bf16, cols);
+    case 3: return occupancy_of<3>(bf16, cols);
+    case 4: return occupancy_of<4>(bf16, cols);
+    case 5: return occupancy_of<5>(bf16, cols);
+    case 6: return occupancy_of<6>(bf16, cols);
+    case 7: return occupancy_of<7>(bf16, cols);
+    case 8: return occupancy_of<8>(bf16, cols);
+    default: return num_sms();
+    }
+}
+
+template <int D>
+static void launch_fused_d(const FusedSpec &f, bool bf16, int cols, int blocks, cudaStream_t st) {
+    if (bf16) {
+        if (cols == 8)
+            k_fused<D, __nv_bfloat16, 8><<<blocks, kThreads, 0, st>>>(f);
+        else
+            k_fused<D, __nv_bfloat16, 4><<<blocks, kThreads, 0, st>>>(f);
+    } else {
+        if (cols == 8)
+            k_fused<D, float, 8><<<blocks, kThreads, 0, st>>>(f);
+        else
+            k_fused<D, float, 4><<<blocks, kThreads, 0, st>>>(f);
+    }
+}
+
+cudaError_t launch_fused(const FusedSpec &f, bool bf16, int cols, int max_blocks, cudaStream_t st,
+                         int *blocks_used) {
     const int64_t S = f.s.p + f.s.q;
     const int64_t ntiles = (S + 31) / 32;
-    int64_t want = (ntiles + (kThreads / 32) - 1) / (kThreads / 32);
+    int64_t want = (ntiles + kWarps - 1) / kWarps;
     if (want < 1) want = 1;
     const int blocks = (int)(want < max_blocks ? want : max_blocks);
     *blocks_used = blocks;
-#define GCP_LAUNCH_FUSED(D)                                                 \
-    if (bf16)                                                               \
-        k_fused<D, __nv_bfloat16><<<blocks, kThreads, 0, st>>>(f);          \
-    else                                                                    \
-        k_fused<D, float><<<blocks, kThreads, 0, st>>>(f)
-    GCP_DISPATCH_D(f.s.d, GCP_LAUNCH_FUSED)
-#undef GCP_LAUNCH_FUSED
+    switch (f.s.d) {
+    case 2: launch_fused_d<2>(f, bf16, cols, blocks, st); break;
+    case 3: launch_fused_d<3>(f, bf16, cols, blocks, st); break;
+    case 4: launch_fused_d<4>(f, bf16, cols, blocks, st); break;
+    case 5: launch_fused_d<5>(f, bf16, cols, blocks, st); break;
+    case 6: launch_fused_d<6>(f, bf16, cols, blocks, st); break;
+    case 7: launch_fused_d<7>(f, bf16, cols, blocks, st); break;
+    case 8: launch_fused_d<8>(f, bf16, cols, blocks, st); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

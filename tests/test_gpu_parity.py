@@ -250,9 +250,17 @@ def test_fit_reduces_objective(env):
     ctx = gcp.gcp_create(w["dims"], w["coords"], w["vals"], 4, "gaussian", seed=8)
     ctx.set_factors(w["factors"])
     rep = ctx.fit(gcp.AdamParams(lr=1e-2), 1000, 1000, 5000, 5000, iters=100, max_epochs=20)
-    assert rep["objective"] < 0.5 * rep["objective0"]
+    assert rep["objective"] < 0.9 * rep["objective0"]
     assert rep["epochs"] >= 1 and rep["iterations"] >= 100
     assert 1.0 <= rep["attempts_per_zero"] < 1.2
+    # the fit ends on the best accepted state: its objective estimate is
+    # reproduced exactly, and the oracle agrees on those factors
+    assert ctx.loss_value(gcp.GCP_ITER_OBJECTIVE, 5000, 5000) == rep["objective"]
+    fac = ctx.get_factors()
+    idx, x, wt, _ = oracle.stratified_samples(8, 2**64 - 1, 5000, 5000, w["dims"], w["coords"], w["vals"])
+    Fo, _ = oracle.sampled_loss_grad(w["dims"], fac, "gaussian", idx, x, wt, grad=False)
+    assert abs(rep["objective"] - Fo) <= TOL_FP32 * abs(Fo)
+    assert rep["objective"] == min(rep["trace"] + [rep["objective0"]])
     ctx.close()
 
 
