@@ -93,6 +93,8 @@ typedef struct {
     uint64_t seed;        /* Philox key word 0                                             */
     void *stream;         /* cudaStream_t for all work of the context; NULL = default     */
     double hash_max_load; /* nonzero hash set load bound in (0, 0.5]; 0 selects 0.3        */
+    int32_t lane_cols;    /* factor columns per GPU lane: 4 or 8; 0 picks 4 for rank <= 32 */
+    int32_t reserved;
 } gcp_options;
 
 typedef struct {
@@ -133,7 +135,7 @@ typedef struct gcp_ctx gcp_ctx;
 typedef struct gcp_batch gcp_batch;
 
 /* Fill *opt with the defaults: FP32 factors, atomic MTTKRP, stratified
- * sampling, 64 attempts, seed 0, default stream, load 0.3. */
+ * sampling, 64 attempts, seed 0, default stream, load 0.3, lane_cols 0. */
 void gcp_options_default(gcp_options *opt);
 
 /* Create a context for a sparse tensor (Sec. 3.1.1: COO list of N tuples and
@@ -191,6 +193,7 @@ gcp_status gcp_reset_adam(gcp_ctx *ctx);
  * and leaves that sample's coordinates at the last candidate. */
 gcp_status gcp_sample(gcp_ctx *ctx, uint64_t iter, int64_t p, int64_t q, int32_t *idx_out,
                       float *x_out, float *w_out);
+/* All sampling calls take p, q >= 0 with p + q < 2^31 (GCP_ERR_ARG otherwise). */
 
 /* Sampled loss estimate F~ = sum_s w_s f(x_s, m_s) of iteration `iter`
  * (Eq. gcp-model on the stratified sample), reduced in FP64, written to the

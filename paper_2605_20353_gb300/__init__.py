@@ -40,7 +40,7 @@ class GcpError(RuntimeError):
 class gcp_options(ctypes.Structure):
     _fields_ = [("factor_dtype", ctypes.c_int32), ("mttkrp", ctypes.c_int32), ("sampling", ctypes.c_int32),
                 ("max_attempts", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p),
-                ("hash_max_load", ctypes.c_double)]
+                ("hash_max_load", ctypes.c_double), ("lane_cols", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class gcp_adam_params(ctypes.Structure):
@@ -280,7 +280,7 @@ class GcpContext:
         return d
 
 
-def _options(dtype, mttkrp, sampling, seed, stream, max_attempts, hash_max_load):
+def _options(dtype, mttkrp, sampling, seed, stream, max_attempts, hash_max_load, lane_cols=0):
     opt = gcp_options()
     load().gcp_options_default(ctypes.byref(opt))
     opt.factor_dtype = DTYPES[dtype]
@@ -290,17 +290,18 @@ def _options(dtype, mttkrp, sampling, seed, stream, max_attempts, hash_max_load)
     opt.stream = _stream_handle(stream)
     opt.max_attempts = max_attempts
     opt.hash_max_load = hash_max_load
+    opt.lane_cols = lane_cols
     return opt
 
 
 def gcp_create(dims, coords, vals, rank, loss, dtype="fp32", mttkrp="atomic", sampling="stratified", seed=0,
-               stream=None, max_attempts=64, hash_max_load=0.3) -> GcpContext:
+               stream=None, max_attempts=64, hash_max_load=0.3, lane_cols=0) -> GcpContext:
     """Sparse tensor context: coords (nnz x d int32) and vals (nnz float32) on the host."""
     lib = load()
     d = np.ascontiguousarray(dims, dtype=np.int64)
     c = np.ascontiguousarray(coords, dtype=np.int32)
     v = np.ascontiguousarray(vals, dtype=np.float32)
-    opt = _options(dtype, mttkrp, sampling, seed, stream, max_attempts, hash_max_load)
+    opt = _options(dtype, mttkrp, sampling, seed, stream, max_attempts, hash_max_load, lane_cols)
     h = ctypes.c_void_p()
     rc = lib.gcp_create(len(d), d.ctypes.data, len(v), c.ctypes.data, v.ctypes.data, rank, LOSSES[loss],
                         ctypes.byref(opt), ctypes.byref(h))
@@ -308,13 +309,13 @@ def gcp_create(dims, coords, vals, rank, loss, dtype="fp32", mttkrp="atomic", sa
     return GcpContext(h.value, d, rank, loss, dtype, stream)
 
 
-def gcp_create_dense(dims, X, rank, loss, dtype="fp32", seed=0, stream=None) -> GcpContext:
+def gcp_create_dense(dims, X, rank, loss, dtype="fp32", seed=0, stream=None, lane_cols=0) -> GcpContext:
     """Dense tensor context; X is a host numpy array or a device tensor."""
     lib = load()
     d = np.ascontiguousarray(dims, dtype=np.int64)
     if isinstance(X, np.ndarray):
         X = np.ascontiguousarray(X, dtype=np.float32)
-    opt = _options(dtype, "atomic", "uniform", seed, stream, 64, 0.3)
+    opt = _options(dtype, "atomic", "uniform", seed, stream, 64, 0.3, lane_cols)
     h = ctypes.c_void_p()
     _check(lib.gcp_create_dense(len(d), d.ctypes.data, _ptr(X), rank, LOSSES[loss], ctypes.byref(opt),
                                 ctypes.byref(h)), None)

@@ -173,6 +173,8 @@ gcp_status init_common(gcp_ctx *c, int32_t ndim, const int64_t *dims, int32_t ra
     while (Rp < rank) Rp <<= 1;
     c->Rp = Rp;
     c->cols = Rp >= 64 ? 8 : 4;
+    if (c->opt.lane_cols == 4 || (c->opt.lane_cols == 8 && Rp >= 8)) c->cols = c->opt.lane_cols;
+    else if (c->opt.lane_cols != 0) return fail(nullptr, GCP_ERR_ARG, "lane_cols must be 0, 4 or 8");
     int L = Rp / c->cols, log2L = 0;
     while ((1 << log2L) < L) ++log2L;
     c->log2L = log2L;
@@ -241,7 +243,7 @@ void weights(const gcp_ctx *c, int64_t p, int64_t q, double &w_nz, double &w_z) 
 gcp_status check_counts(gcp_ctx *c, int64_t p, int64_t q) {
     if (p < 0 || q < 0) return fail(c, GCP_ERR_ARG, "negative sample count");
     if (c->dense && q != 0) return fail(c, GCP_ERR_ARG, "dense tensors take p uniform samples and q = 0");
-    if (p + q > ((int64_t)1 << 40)) return fail(c, GCP_ERR_ARG, "too many samples");
+    if (p + q >= ((int64_t)1 << 31)) return fail(c, GCP_ERR_ARG, "p + q must be below 2^31 per call");
     return GCP_OK;
 }
 
@@ -263,7 +265,7 @@ gcp_status run_fused(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad,
     f.w_z = (float)w_z;
     f.dscale = dscale;
     f.partials = c->partials;
-    f.hot_slot = c->hot_slot;
+    for (int k = 0; k < c->d; ++k) f.small_base[k] = c->small_base[k];
     f.Grep = c->Grep;
     f.Htot = c->Htot;
     if (grad) GCP_CUDA(c, cudaMemsetAsync(c->G, 0, (size_t)c->total_rows * c->Rp * 4, c->st));
@@ -303,29 +305,39 @@ gcp_status refresh_bf16(gcp_ctx *c) {
     return GCP_OK;
 }
 
-// Rows that receive many gradient reductions per call get replicas: rows
-// holding at least 1/512 of the nonzeros (hit by that share of the nonzero
-// samples) and every row of a mode with at most 512 rows (hit by 1/I_k of
-// the zero or uniform samples); at most 4096 rows, hottest first.
+// Rows that receive many gradient reductions per call get replicas: every
+// row of a mode with at most 512 rows (each is hit by 1/I_k of the drawn
+// cells), with contiguous slots so drawn cells find theirs by arithmetic;
+// then, for larger modes, rows holding at least 1/512 of the nonzeros (hit
+// by that share of the nonzero samples), at most 256 per mode, hottest
+// first.  A nonzero record stores the slots of its rows.
 gcp_status setup_hot_rows(gcp_ctx *c, const std::vector<int64_t> &counts) {
-    std::vector<std::pair<double, int>> cand;
+    std::vector<int> slot((size_t)c->total_rows, -1), row;
     for (int k = 0; k < c->d; ++k) {
-        const double uni = 1.0 / (double)c->dims[k];
+        c->small_base[k] = -1;
+        if (c->dims[k] > 512) continue;
+        c->small_base[k] = (int)row.size();
         for (int64_t i = 0; i < c->dims[k]; ++i) {
-            const int row = (int)(c->rowoff[k] + i);
-            const double nz = counts.empty() ? 0.0 : (double)counts[row] / (double)c->nnz;
-            if (nz * 512.0 >= 1.0 || c->dims[k] <= 512) cand.push_back({nz > uni ? nz : uni, row});
+            slot[(size_t)(c->rowoff[k] + i)] = (int)row.size();
+            row.push_back((int)(c->rowoff[k] + i));
         }
     }
-    std::stable_sort(cand.begin(), cand.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
-    if (cand.size() > 4096) cand.resize(4096);
-    c->Htot = (int)cand.size();
-    if (c->Htot == 0) return GCP_OK;
-    std::vector<int> slot((size_t)c->total_rows, -1), row(cand.size());
-    for (size_t s = 0; s < cand.size(); ++s) {
-        slot[cand[s].second] = (int)s;
-        row[s] = cand[s].second;
+    for (int k = 0; k < c->d && !counts.empty(); ++k) {
+        if (c->dims[k] <= 512) continue;
+        std::vector<std::pair<int64_t, int>> hot;
+        for (int64_t i = 0; i < c->dims[k]; ++i) {
+            const int64_t n = counts[(size_t)(c->rowoff[k] + i)];
+            if ((double)n * 512.0 >= (double)c->nnz) hot.push_back({n, (int)(c->rowoff[k] + i)});
+        }
+        std::stable_sort(hot.begin(), hot.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
+        if (hot.size() > 256) hot.resize(256);
+        for (const auto &h : hot) {
+            slot[(size_t)h.second] = (int)row.size();
+            row.push_back(h.second);
+        }
     }
+    c->Htot = (int)row.size();
+    if (c->Htot == 0) return GCP_OK;
     const size_t rep_bytes = (size_t)gcpk::kReplicas * c->Htot * c->Rp * 4;
     cudaError_t e;
     if ((e = cudaMalloc(&c->hot_slot, slot.size() * 4)) || (e = cudaMalloc(&c->hot_row, row.size() * 4)) ||
@@ -417,8 +429,8 @@ gcp_status gcp_create(int32_t ndim, const int64_t *dims, int64_t nnz, const int3
     if ((e = cudaMemsetAsync(c->hkeys, 0xFF, cap * 8, c->st)) ||
         (e = cudaMemcpyAsync(dcoords, coords, (size_t)nnz * ndim * 4, cudaMemcpyHostToDevice, c->st)) ||
         (e = cudaMemcpyAsync(dvals, vals, (size_t)nnz * 4, cudaMemcpyHostToDevice, c->st)) ||
-        (e = gcpk::launch_build_records(dcoords, dvals, nnz, ndim, c->stride, c->rec_words, c->rec, c->hkeys,
-                                        c->hbmask, c->status, c->st)) ||
+        (e = gcpk::launch_build_records(dcoords, dvals, nnz, ndim, c->stride, c->rowoff, c->hot_slot,
+                                        c->rec_words, c->rec, c->hkeys, c->hbmask, c->status, c->st)) ||
         (e = cudaStreamSynchronize(c->st))) {
         cudaFree(dcoords);
         cudaFree(dvals);

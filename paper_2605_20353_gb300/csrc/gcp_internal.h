@@ -43,7 +43,8 @@ struct FusedSpec {
     float w_nz, w_z;                // per-sample weights (FP32 copies)
     const float *dscale;            // gradient scale (device) or null
     double *partials;               // per block: sum f over nonzero / zero samples, attempts, -
-    const int *hot_slot;            // row -> replica slot, -1 = not replicated (null = none)
+    int small_base[GCP_MAX_NDIM];   // replica slot of row 0 of a mode whose rows all have
+                                    // slots (contiguous), else -1; used for drawn cells
     float *Grep;                    // kReplicas x Htot x Rp replica rows (zero between calls)
     int Htot;                       // replicated rows
 };
@@ -60,8 +61,9 @@ struct LaunchCfg {
 // ---------------------------------------------------------------- kernels
 // All launches are asynchronous on `st`; device errors go to the status word.
 cudaError_t launch_build_records(const int32_t *coords, const float *vals, int64_t nnz, int d,
-                                 const uint64_t *stride, int rec_words, int32_t *rec, uint64_t *hkeys,
-                                 uint64_t hbmask, int *status, cudaStream_t st);
+                                 const uint64_t *stride, const int64_t *rowoff, const int *hot_slot,
+                                 int rec_words, int32_t *rec, uint64_t *hkeys, uint64_t hbmask, int *status,
+                                 cudaStream_t st);
 cudaError_t launch_sample(const SampleSpec &s, int32_t *idx_out, float *x_out, float *w_out, float w_nz,
                           float w_z, cudaStream_t st);
 cudaError_t launch_fused(const FusedSpec &f, bool bf16, int cols, int max_blocks, cudaStream_t st,
@@ -111,8 +113,9 @@ struct gcp_ctx {
     double *h_loss = nullptr;     // pinned mirror of dloss
 
     // hot-row replicas of the gradient
-    int *hot_slot = nullptr;      // [total_rows]
-    int *hot_row = nullptr;       // [Htot]
+    int *hot_slot = nullptr;      // [total_rows] row -> replica slot or -1
+    int *hot_row = nullptr;       // [Htot] slot -> row
+    int small_base[GCP_MAX_NDIM] = {0};
     float *Grep = nullptr;        // [kReplicas x Htot x Rp]
     int Htot = 0;
 
@@ -132,10 +135,14 @@ struct gcp_ctx {
 };
 
 namespace gcpk {
-// Words per packed nonzero record: d int32 coordinates then the value's
-// bits, padded to 16, 32 or 64 bytes so one record sits in one or two
-// 32-byte sectors and loads as 16-byte vectors.
-__host__ __device__ constexpr int rec_words_for(int d) { return d + 1 <= 4 ? 4 : (d + 1 <= 8 ? 8 : 16); }
+// Words per packed nonzero record: d int32 coordinates, the value's bits,
+// then the d 16-bit gradient replica slots of its rows (0xFFFF = none),
+// padded to 16, 32 or 64 bytes so a record sits in whole 32-byte sectors
+// and loads as 16-byte vectors.
+__host__ __device__ constexpr int rec_words_for(int d) {
+    return d + 1 + (d + 1) / 2 <= 4 ? 4 : (d + 1 + (d + 1) / 2 <= 8 ? 8 : 16);
+}
+constexpr unsigned kNoSlot = 0xFFFFu;
 }  // namespace gcpk
 
 // Deterministic MTTKRP gradient of one sample set (gcp_mttkrp_det.cu): fills

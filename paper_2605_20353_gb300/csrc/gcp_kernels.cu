@@ -24,6 +24,10 @@ namespace gcpk {
 
 constexpr int kThreads = 256;
 
+struct RowOffsets {
+    int64_t off[GCP_MAX_NDIM];
+};
+
 template <int D>
 __device__ __forceinline__ void draw_tuple(const SampleSpec &S, uint64_t stream, uint64_t j, uint64_t sub0,
                                            int32_t (&idx)[D]) {
@@ -120,7 +124,7 @@ constexpr int kWarps = kThreads / 32;
 
 template <int D, typename TF, int COLS>
 __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) k_fused(const FusedSpec P) {
-    constexpr int SW = rec_words_for(D);  // words per staged sample: coordinates, value, padding
+    constexpr int SW = rec_words_for(D);  // words per staged sample: coordinates, value, replica slots
     constexpr int NQ = COLS / 4;          // quads of columns per lane
     __shared__ __align__(16) int32_t s_slot[2][kWarps][32][SW];
     __shared__ __align__(16) uint64_t s_bkt[2][kWarps][32][4];
@@ -136,10 +140,11 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
     int col[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) col[q] = q * (P.Rp >> 1) + 4 * glane;
-    const int64_t S = P.s.p + P.s.q;
-    const int64_t ntiles = (S + 31) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int p = (int)P.s.p;  // sample counts of one call are below 2^31
+    const int S = (int)(P.s.p + P.s.q);
+    const int ntiles = (S + 31) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const TF *__restrict__ F = static_cast<const TF *>(P.F);
     const float scale = P.dscale ? __ldg(P.dscale) : 1.0f;
     const bool semi = P.s.sampling == GCP_SAMPLING_SEMI_STRATIFIED;
@@ -149,10 +154,10 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
     double acc_nz = 0.0, acc_z = 0.0;
     int attempts = 0;
 
-    // A1: start the draw of sample s into stage `st`; returns the key of a
-    // stratified zero candidate (kEmpty otherwise).
-    auto issue = [&](int64_t tile, int st) -> uint64_t {
-        const int64_t s = (tile << 5) + lane;
+    // A1: start the draw of this lane's sample of `tile` into stage `st`;
+    // returns the key of a stratified zero candidate (kEmpty otherwise).
+    auto issue = [&](int tile, int st) -> uint64_t {
+        const int s = (tile << 5) + lane;
         int32_t *slot = s_slot[st][warp][lane];
         if (tile >= ntiles || s >= S) return kEmpty;
         if (uniform) {
@@ -163,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
             cp_async4(slot + D, P.s.dense + linear_of<D>(P.s, idx));
             return kEmpty;
         }
-        if (s < P.s.p) {
+        if (s < p) {
             const U64x4 w = philox4x64_10((uint64_t)s, 0, P.s.iter, 0, P.s.seed, kStreamNonzero);
             const int32_t *rec = P.s.rec + map_range(w.v[0], (uint64_t)P.s.nnz) * SW;
 #pragma unroll
@@ -171,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
             return kEmpty;
         }
         int32_t idx[D];
-        draw_tuple<D>(P.s, semi ? kStreamSemiZero : kStreamZero, (uint64_t)(s - P.s.p), 0, idx);
+        draw_tuple<D>(P.s, semi ? kStreamSemiZero : kStreamZero, (uint64_t)(s - p), 0, idx);
 #pragma unroll
         for (int k = 0; k < D; ++k) slot[k] = idx[k];
         slot[D] = 0;  // x = 0.0f
@@ -184,8 +189,8 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
     };
 
     // A2: finish the draw of stage `st`; returns whether the sample exists.
-    auto finish = [&](int64_t tile, int st, uint64_t key) -> bool {
-        const int64_t s = (tile << 5) + lane;
+    auto finish = [&](int tile, int st, uint64_t key) -> bool {
+        const int s = (tile << 5) + lane;
         if (s >= S) return false;
         if (key == kEmpty) return true;  // nonzero, semi-stratified or dense draw
         const ulonglong2 lo = *reinterpret_cast<const ulonglong2 *>(&s_bkt[st][warp][lane][0]);
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
         }
         // rejected: redraw until a candidate is absent (Sec. 3.1.1)
         int32_t *slot = s_slot[st][warp][lane];
-        const uint64_t j = (uint64_t)(s - P.s.p);
+        const uint64_t j = (uint64_t)(s - p);
         for (int a = 1; h == 1 && a < P.s.max_attempts; ++a) {
             int32_t idx[D];
             draw_tuple<D>(P.s, kStreamZero, j, 4 * (uint64_t)a, idx);
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
         return false;
     };
 
-    int64_t tile = warp0;
+    int tile = warp0;
     uint64_t key_next = issue(tile, 0);
     cp_async_commit();
     for (int st = 0; tile < ntiles; tile += nwarps, st ^= 1) {
@@ -233,7 +238,9 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
         const unsigned okmask = __ballot_sync(0xFFFFFFFFu, ok);
         __syncwarp();  // every lane's staged sample is visible to the warp
 
-        // phase B: one sample per group
+        // phase B: one sample per group; the group leader keeps FP32 loss
+        // sums of the tile, added to the FP64 totals once per tile
+        float tf_nz = 0.0f, tf_z = 0.0f;
         for (int it = 0; it < L; ++it) {
             const int src = it * ngrp + grp;
             if (!((okmask >> src) & 1u)) continue;  // uniform within the group
@@ -242,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
 #pragma unroll
             for (int k = 0; k < D; ++k) ii[k] = slot[k];
             const float xs = __int_as_float(slot[D]);
-            const bool is_nz = ((tile << 5) + src) < P.s.p;
+            const bool is_nz = !uniform && ((tile << 5) + src) < p;
 
             int off[D];
             float a[D][COLS];
@@ -272,21 +279,25 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
                 f -= f0;
                 df -= df0;
             }
-            if (glane == 0) {
-                if (is_nz)
-                    acc_nz += (double)f;
-                else
-                    acc_z += (double)f;
-            }
+            if (is_nz || uniform)
+                tf_nz += f;
+            else
+                tf_z += f;
             if (P.G) {
-                const float y = (is_nz ? P.w_nz : P.w_z) * df * scale;
+                const float y = ((is_nz || uniform) ? P.w_nz : P.w_z) * df * scale;
                 float pre[COLS];
 #pragma unroll
                 for (int v = 0; v < COLS; ++v) pre[v] = y;
 #pragma unroll
                 for (int n = 0; n < D; ++n) {
-                    const int hs = P.hot_slot ? __ldg(P.hot_slot + P.rowoff[n] + ii[n]) : -1;
-                    float *g = hs >= 0 ? grep + hs * P.Rp : P.G + off[n];
+                    // replica slot: stored in a nonzero's record; for drawn
+                    // cells, rows of fully replicated modes only
+                    unsigned hs;
+                    if (is_nz)
+                        hs = ((unsigned)slot[D + 1 + n / 2] >> (16 * (n & 1))) & 0xFFFFu;
+                    else
+                        hs = P.small_base[n] >= 0 ? (unsigned)(P.small_base[n] + ii[n]) : kNoSlot;
+                    float *g = hs != kNoSlot ? grep + (int)hs * P.Rp : P.G + off[n];
 #pragma unroll
                     for (int q = 0; q < NQ; ++q)
                         red_add_v4(g + col[q], pre[4 * q] * suf[n][4 * q], pre[4 * q + 1] * suf[n][4 * q + 1],
@@ -295,6 +306,10 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
                     for (int v = 0; v < COLS; ++v) pre[v] *= a[n][v];
                 }
             }
+        }
+        if (glane == 0) {
+            acc_nz += (double)tf_nz;
+            acc_z += (double)tf_z;
         }
     }
     cp_async_wait<0>();
@@ -322,8 +337,9 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
     }
 }
 
-// G(hot row) = sum over replicas, then the replicas are cleared for the
-// next call (fixed replica order).
+// G(hot row) += sum over replicas, then the replicas are cleared for the
+// next call (fixed replica order).  G may already hold contributions of
+// drawn cells to a replicated row of a large mode.
 __global__ void k_fold_replicas(float *__restrict__ G, float *__restrict__ Grep, const int *__restrict__ hot_row,
                                 int Htot, int Rp) {
     const int64_t n = (int64_t)Htot * Rp;
@@ -336,7 +352,7 @@ __global__ void k_fold_replicas(float *__restrict__ G, float *__restrict__ Grep,
             t += *p;
             *p = 0.0f;
         }
-        G[(int64_t)hot_row[slot] * Rp + col] = t;
+        G[(int64_t)hot_row[slot] * Rp + col] += t;
     }
 }
 
@@ -382,18 +398,21 @@ __global__ void __launch_bounds__(kThreads) k_sample(const SampleSpec S, int32_t
 
 // ------------------------------------------------------ nonzero records
 __global__ void k_build_records(const int32_t *__restrict__ coords, const float *__restrict__ vals, int64_t nnz,
-                                int d, SampleSpec S, int rec_words, int32_t *rec, uint64_t *hkeys,
-                                uint64_t hbmask, int *status) {
+                                int d, SampleSpec S, RowOffsets ro, const int *__restrict__ hot_slot, int rec_words,
+                                int32_t *rec, uint64_t *hkeys, uint64_t hbmask, int *status) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
         uint64_t L = 0;
         int32_t *r = rec + e * rec_words;
+        for (int k = d + 1; k < rec_words; ++k) r[k] = 0;
         for (int k = 0; k < d; ++k) {
             const int32_t c = coords[e * d + k];
             r[k] = c;
             L += (uint64_t)c * S.stride[k];
+            const int hs = hot_slot ? hot_slot[ro.off[k] + c] : -1;
+            const unsigned code = hs >= 0 ? (unsigned)hs : kNoSlot;
+            r[d + 1 + k / 2] |= (int32_t)(code << (16 * (k & 1)));
         }
         r[d] = __float_as_int(vals[e]);
-        for (int k = d + 1; k < rec_words; ++k) r[k] = 0;
         const int rc = hash_insert(hkeys, hbmask, L);
         if (rc) atomicOr(status, rc);
     }
@@ -442,13 +461,18 @@ static int elementwise_blocks(int64_t n) {
 }
 
 cudaError_t launch_build_records(const int32_t *coords, const float *vals, int64_t nnz, int d,
-                                 const uint64_t *stride, int rec_words, int32_t *rec, uint64_t *hkeys,
-                                 uint64_t hbmask, int *status, cudaStream_t st) {
+                                 const uint64_t *stride, const int64_t *rowoff, const int *hot_slot,
+                                 int rec_words, int32_t *rec, uint64_t *hkeys, uint64_t hbmask, int *status,
+                                 cudaStream_t st) {
     SampleSpec S{};
     S.d = d;
-    for (int k = 0; k < d; ++k) S.stride[k] = stride[k];
-    k_build_records<<<elementwise_blocks(nnz), kThreads, 0, st>>>(coords, vals, nnz, d, S, rec_words, rec, hkeys,
-                                                                   hbmask, status);
+    RowOffsets ro{};
+    for (int k = 0; k < d; ++k) {
+        S.stride[k] = stride[k];
+        ro.off[k] = rowoff[k];
+    }
+    k_build_records<<<elementwise_blocks(nnz), kThreads, 0, st>>>(coords, vals, nnz, d, S, ro, hot_slot, rec_words,
+                                                                   rec, hkeys, hbmask, status);
     return cudaGetLastError();
 }
 
