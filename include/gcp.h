@@ -49,7 +49,7 @@ extern "C" {
 #define GCP_MAX_NDIM 8
 #define GCP_MAX_RANK 128
 /* Iteration number whose sample set is the fixed objective-estimate set
- * used by gcp_fit (Sec. 4.1: a fixed number of objective samples). */
+ * used by gcp_fit (Sec. 5.1: a fixed number of objective samples). */
 #define GCP_ITER_OBJECTIVE 0xFFFFFFFFFFFFFFFFull
 
 typedef enum {
@@ -231,7 +231,7 @@ gcp_status gcp_sync(gcp_ctx *ctx);
  * or max_epochs.  report may be NULL. */
 gcp_status gcp_fit(gcp_ctx *ctx, const gcp_fit_params *prm, gcp_fit_report *report);
 
-/* Kernel timing (the per-phase runtime breakdown of Sec. 4.1, on one GPU).
+/* Kernel timing (the per-phase runtime breakdown of Sec. 5.1, on one GPU).
  * While enabled, every launch of the fused sampling/model/loss/MTTKRP kernel
  * on the context's stream is bracketed by CUDA events on that stream.
  * gcp_profile_read synchronises, returns the summed kernel milliseconds and
