@@ -162,8 +162,9 @@ gcp_status gcp_create_dense(int32_t ndim, const int64_t *dims, const float *X, i
 /* Release every resource of the context (synchronises its stream). NULL ok. */
 void gcp_destroy(gcp_ctx *ctx);
 
-/* Last error message of the context (or of the last failed create when ctx
- * is NULL); never NULL; valid until the next call on that context. */
+/* Last error message of the context (or, when ctx is NULL, of the last
+ * failed call of this thread that has no context); never NULL; valid until
+ * the next call on that context. */
 const char *gcp_last_error(const gcp_ctx *ctx);
 
 /* Shape queries. */
@@ -239,6 +240,37 @@ gcp_status gcp_fit(gcp_ctx *ctx, const gcp_fit_params *prm, gcp_fit_report *repo
  * default; enabling costs two event records per launch. */
 gcp_status gcp_profile(gcp_ctx *ctx, int32_t enable);
 gcp_status gcp_profile_read(gcp_ctx *ctx, double *kernel_ms, int64_t *launches);
+
+/* Sampled loss and gradient of a caller-supplied sample list, allocating
+ * nothing.  The paper has no counterpart: it exists for callers that cannot
+ * allocate device memory -- code that runs under a device-memory budget
+ * fixed at start-up, such as a host framework that owns every allocation
+ * through its own pool, or a long-running service that must not grow its
+ * footprint.  The caller passes every input and output; the only scratch
+ * (one loss partial per block of 2048 samples) is a file-scope device array
+ * of the library, 128 KB, held by every GPU that loads the library until the
+ * process exits.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.
+ *   dims[ndim] (host) mode sizes; rank 1..128; loss a gcp_loss_t;
+ *   idx (device, nsamples x ndim int32 row-major), x and w (device, nsamples
+ *   floats): sample s is cell idx[s], value x[s], weight w[s];
+ *   A (device, flat FP32 factors, see Conventions, unpadded rank columns);
+ *   G (device, same layout, overwritten) receives
+ *     sum_s w_s f'(x_s, m_s) prod_{k!=n} A_k(i_k,:) in each mode's rows;
+ *   loss_out (device, 2 doubles): [0] = sum_s w_s f(x_s, m_s) (FP64, fixed
+ *   order), [1] = samples skipped because a coordinate was out of range;
+ *   stream a cudaStream_t (NULL = default stream).
+ * nsamples may be at most GCP_NOALLOC_MAX_SAMPLES; larger counts are
+ * rejected with GCP_ERR_ARG (message from gcp_last_error(NULL)) and must be
+ * split over several calls.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call on a device
+ * shares the array: calls whose kernels overlap on the GPU race and must be
+ * ordered by the caller (one stream, or events).  Asynchronous. */
+#define GCP_NOALLOC_MAX_SAMPLES 16777216LL
+gcp_status gcp_grad_samples_noalloc(int32_t ndim, const int64_t *dims, int32_t rank, int32_t loss,
+                                    int64_t nsamples, const int32_t *idx, const float *x, const float *w,
+                                    const float *A, float *G, double *loss_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -91,6 +91,7 @@ SIGNATURES = {
     "gcp_fit": (_i32, [_vp, ctypes.POINTER(gcp_fit_params), ctypes.POINTER(gcp_fit_report)]),
     "gcp_profile": (_i32, [_vp, _i32]),
     "gcp_profile_read": (_i32, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_i64)]),
+    "gcp_grad_samples_noalloc": (_i32, [_i32, _vp, _i32, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 
@@ -320,6 +321,16 @@ def gcp_create_dense(dims, X, rank, loss, dtype="fp32", seed=0, stream=None, lan
     _check(lib.gcp_create_dense(len(d), d.ctypes.data, _ptr(X), rank, LOSSES[loss], ctypes.byref(opt),
                                 ctypes.byref(h)), None)
     return GcpContext(h.value, d, rank, loss, dtype, stream)
+
+
+def gcp_grad_samples_noalloc(dims, rank, loss, idx, x, w, A, G, loss_out, stream=None):
+    """Loss and gradient of a given sample list with no device allocation
+    (for callers that cannot allocate).  idx/x/w/A/G/loss_out are device
+    tensors; loss_out holds 2 doubles (loss, skipped samples).  Asynchronous."""
+    d = np.ascontiguousarray(dims, dtype=np.int64)
+    _check(load().gcp_grad_samples_noalloc(len(d), d.ctypes.data, rank, LOSSES[loss], int(idx.shape[0]), _ptr(idx),
+                                           _ptr(x), _ptr(w), _ptr(A), _ptr(G), _ptr(loss_out),
+                                           _stream_handle(stream)), None)
 
 
 # C-named conveniences over a context

@@ -351,6 +351,8 @@ gcp_status setup_hot_rows(gcp_ctx *c, const std::vector<int64_t> &counts) {
 
 }  // namespace
 
+void gcpk_set_noctx_error(const char *msg) { g_create_err = msg; }
+
 // =================================================================== ABI
 extern "C" {
 

@@ -148,3 +148,7 @@ constexpr unsigned kNoSlot = 0xFFFFu;
 // Deterministic MTTKRP gradient of one sample set (gcp_mttkrp_det.cu): fills
 // f.G and the loss partials; *blocks = number of partials written.
 gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f, int *blocks);
+
+// Record the message of a failed call that has no context; gcp_last_error(NULL)
+// returns it.
+void gcpk_set_noctx_error(const char *msg);
