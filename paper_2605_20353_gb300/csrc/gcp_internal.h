@@ -47,6 +47,8 @@ struct FusedSpec {
                                     // slots (contiguous), else -1; used for drawn cells
     float *Grep;                    // kReplicas x Htot x Rp replica rows (zero between calls)
     int Htot;                       // replicated rows
+    int32_t *Ycoord;                // materialize mode (G null): per-sample coordinates [S x d]
+    float *Yval;                    //   and gradient-tensor values w f' scale [S] (0 if no sample)
 };
 
 // Rows that many samples hit (Zipf heads, rows of small modes) are

@@ -243,7 +243,15 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
         float tf_nz = 0.0f, tf_z = 0.0f;
         for (int it = 0; it < L; ++it) {
             const int src = it * ngrp + grp;
-            if (!((okmask >> src) & 1u)) continue;  // uniform within the group
+            if (!((okmask >> src) & 1u)) {  // uniform within the group
+                const int sm = (tile << 5) + src;
+                if (P.Yval && glane == 0 && sm < S) {  // no sample: a zero entry at a valid cell
+#pragma unroll
+                    for (int k = 0; k < D; ++k) P.Ycoord[(int64_t)sm * D + k] = s_slot[st][warp][src][k];
+                    P.Yval[sm] = 0.0f;
+                }
+                continue;
+            }
             const int32_t *slot = s_slot[st][warp][src];
             int32_t ii[D];
 #pragma unroll
@@ -283,7 +291,14 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
                 tf_nz += f;
             else
                 tf_z += f;
-            if (P.G) {
+            if (P.Yval) {  // materialize the gradient tensor entry (non-fused MTTKRP input)
+                if (glane == 0) {
+                    const int sm = (tile << 5) + src;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) P.Ycoord[(int64_t)sm * D + k] = ii[k];
+                    P.Yval[sm] = ((is_nz || uniform) ? P.w_nz : P.w_z) * df * scale;
+                }
+            } else if (P.G) {
                 const float y = ((is_nz || uniform) ? P.w_nz : P.w_z) * df * scale;
                 float pre[COLS];
 #pragma unroll
@@ -339,21 +354,30 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
 
 // G(hot row) += sum over replicas, then the replicas are cleared for the
 // next call (fixed replica order).  G may already hold contributions of
-// drawn cells to a replicated row of a large mode.
-__global__ void k_fold_replicas(float *__restrict__ G, float *__restrict__ Grep, const int *__restrict__ hot_row,
-                                int Htot, int Rp) {
-    const int64_t n = (int64_t)Htot * Rp;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int slot = (int)(e / Rp), col = (int)(e % Rp);
+// drawn cells to a replicated row of a large mode.  All kReplicas loads of
+// an element are issued before any store.
+__device__ __forceinline__ void fold_range(float *__restrict__ G, float *__restrict__ Grep,
+                                           const int *__restrict__ hot_row, int Htot, int Rp, int64_t first,
+                                           int64_t stride) {
+    const int64_t n = (int64_t)Htot * Rp, plane = (int64_t)Htot * Rp;
+    for (int64_t e = first; e < n; e += stride) {
+        float v[kReplicas];
+#pragma unroll
+        for (int r = 0; r < kReplicas; ++r) v[r] = Grep[r * plane + e];
         float t = 0.0f;
-#pragma unroll 8
-        for (int r = 0; r < kReplicas; ++r) {
-            float *p = Grep + ((int64_t)r * Htot + slot) * Rp + col;
-            t += *p;
-            *p = 0.0f;
-        }
+#pragma unroll
+        for (int r = 0; r < kReplicas; ++r) t += v[r];
+#pragma unroll
+        for (int r = 0; r < kReplicas; ++r) Grep[r * plane + e] = 0.0f;
+        const int slot = (int)(e / Rp), col = (int)(e % Rp);
         G[(int64_t)hot_row[slot] * Rp + col] += t;
     }
+}
+
+__global__ void k_fold_replicas(float *__restrict__ G, float *__restrict__ Grep, const int *__restrict__ hot_row,
+                                int Htot, int Rp) {
+    fold_range(G, Grep, hot_row, Htot, Rp, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+               (int64_t)gridDim.x * blockDim.x);
 }
 
 // Fixed-order reduction of the block partials (one block).

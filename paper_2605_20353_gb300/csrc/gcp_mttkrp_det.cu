@@ -1,7 +1,438 @@
-// gcp_mttkrp_det.cu -- deterministic (sort-by-row) MTTKRP variant.
+// gcp_mttkrp_det.cu -- deterministic all-mode sampled MTTKRP.
+//
+// The gradient of a sample set is G_n(i_n,:) = sum_s y_s prod_{k!=n}
+// A_k(i_k,:) (Eq. gcp-gradient on the sampled gradient tensor).  The atomic
+// variant adds these terms in whatever order the hardware applies the
+// reductions.  This variant fixes the order, so G is bit-identical from run
+// to run, in the spirit of the permutation-based MTTKRP of Sec. 3.1.2:
+//   1. the fused kernel in materialize mode writes every sample's cell and
+//      value y_s = w f'(x_s, m_s) (the non-fused gradient tensor);
+//   2. per mode n, a stable LSD radix sort (8-bit digits) orders the sample
+//      ids by row i_n, ties in sample order;
+//   3. a chunked segmented reduction walks the sorted list in chunks of kChunk
+//      positions, one chunk per group of lanes, recomputing the Khatri-Rao row
+//      products.  A run of equal rows that lies inside one chunk is stored to
+//      G directly; a run that crosses a chunk edge leaves a partial vector,
+//      and the partials (again sorted by row) are reduced the same way, level
+//      after level, until one chunk holds them all.
+// Every step has a fixed shape and order, so the result depends only on the
+// inputs.
+#include <cuda_bf16.h>
+
+#include <utility>
+
+#include "gcp_device.cuh"
 #include "gcp_internal.h"
 
-gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &, int *) {
-    c->err = "deterministic MTTKRP not available";
-    return GCP_ERR_STATE;
+using namespace gcpdev;
+
+namespace {
+
+constexpr int kT = 256;            // threads per block
+constexpr int kTile = 4096;        // keys per radix-sort block
+constexpr int kChunk = 256;        // sorted positions per segmented-reduction chunk
+
+// --------------------------------------------------------------- radix sort
+__global__ void k_radix_hist(const int32_t *__restrict__ keys, int key_stride, int64_t n, int shift,
+                             int32_t *__restrict__ hist, int ntiles) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t first = (int64_t)blockIdx.x * kTile;
+    for (int i = threadIdx.x; i < kTile && first + i < n; i += kT)
+        atomicAdd(&h[(keys[(first + i) * key_stride] >> shift) & 255], 1);
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive prefix sum of n ints in place (one block, fixed order).
+__global__ void k_scan_exclusive(int32_t *a, int64_t n, int32_t *total) {
+    __shared__ int64_t part[kT];
+    const int64_t per = (n + kT - 1) / kT;
+    const int64_t lo = (int64_t)threadIdx.x * per, hi = lo + per < n ? lo + per : n;
+    int64_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += a[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int t = 0; t < kT; ++t) {
+            const int64_t v = part[t];
+            part[t] = run;
+            run += v;
+        }
+        if (total) *total = (int32_t)run;
+    }
+    __syncthreads();
+    int64_t run = part[threadIdx.x];
+    for (int64_t i = lo; i < hi; ++i) {
+        const int32_t v = a[i];
+        a[i] = (int32_t)run;
+        run += v;
+    }
+}
+
+// Stable scatter of one 8-bit digit pass.  Keys of a tile are ranked in
+// index order: rounds of kT keys, warps in order, lanes in order.
+__global__ void k_radix_scatter(const int32_t *__restrict__ keys, int key_stride, const int32_t *__restrict__ vals,
+                                int64_t n, int shift, const int32_t *__restrict__ offsets, int ntiles,
+                                int32_t *__restrict__ keys_out, int32_t *__restrict__ vals_out) {
+    __shared__ int running[256];
+    __shared__ int wcount[kT / 32][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    running[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    for (int w = 0; w < kT / 32; ++w) wcount[w][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t first = (int64_t)blockIdx.x * kTile;
+    for (int r = 0; r < kTile / kT; ++r) {
+        const int64_t i = first + r * kT + threadIdx.x;
+        const bool valid = i < n;
+        int32_t key = 0, val = 0;
+        int digit = 256;  // no digit: never matches a real one
+        if (valid) {
+            key = keys[i * key_stride];
+            val = vals ? vals[i] : (int32_t)i;
+            digit = (key >> shift) & 255;
+        }
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, digit);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wcount[warp][digit] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int pos = running[digit] + rank;
+            for (int w = 0; w < warp; ++w) pos += wcount[w][digit];
+            keys_out[pos] = key;
+            vals_out[pos] = val;
+        }
+        __syncthreads();
+        int add = 0;
+        for (int w = 0; w < kT / 32; ++w) {
+            add += wcount[w][threadIdx.x];
+            wcount[w][threadIdx.x] = 0;
+        }
+        running[threadIdx.x] += add;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------ segmented reduction
+struct SegSpec {
+    int n_mode;        // mode whose gradient rows are reduced
+    int d, Rp, cols, log2L;
+    int rowoff[GCP_MAX_NDIM];
+    const void *F;     // factors read by the kernels (FP32 or BF16)
+    const int32_t *Ycoord;
+    const float *Yval;
+    float *G;
+};
+
+template <typename TF, int NQ>
+__device__ __forceinline__ void load_cols(const TF *F, int off, const int (&col)[NQ], float (&o)[4 * NQ]) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) Quad<TF>::load(F + off + col[q], o + 4 * q);
+}
+
+// Emit one run of equal keys: a run inside the chunk is final (stored to G),
+// a run touching a chunk edge becomes the chunk's left (started earlier) or
+// right (continues later) carry.
+template <int NQ>
+__device__ __forceinline__ void emit_run(float *G, int Rp, int row_base, int key, const float (&acc)[4 * NQ],
+                                         const int (&col)[NQ], bool before, bool after, int chunk, int32_t *ckey,
+                                         float *cvec) {
+    float *dst;
+    if (!before && !after) {
+        dst = G + (int64_t)(row_base + key) * Rp;
+    } else {
+        const int slot = 2 * chunk + (before ? 0 : 1);
+        dst = cvec + (int64_t)slot * Rp;
+        if (col[0] == 0) ckey[slot] = key;  // the group's lane 0 records the row
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+        *reinterpret_cast<float4 *>(dst + col[q]) = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+}
+
+// Level 1: sorted sample ids of one mode -> G rows and edge carries.
+template <typename TF, int COLS>
+__global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32_t *__restrict__ keys,
+                                                    const int32_t *__restrict__ ids, int64_t n, int32_t *ckey,
+                                                    float *cvec) {
+    constexpr int NQ = COLS / 4;
+    const int lane = threadIdx.x & 31;
+    const int L = 1 << P.log2L;
+    const int glane = lane & (L - 1);
+    const int64_t group = ((int64_t)blockIdx.x * kT + threadIdx.x) >> P.log2L;
+    const int64_t ngroups = ((int64_t)gridDim.x * kT) >> P.log2L;
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    const TF *F = static_cast<const TF *>(P.F);
+    int col[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) col[q] = q * (P.Rp >> 1) + 4 * glane;
+    for (int64_t c = group; c < nchunks; c += ngroups) {
+        const int64_t lo = c * kChunk, hi = lo + kChunk < n ? lo + kChunk : n;
+        float acc[COLS];
+#pragma unroll
+        for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
+        int cur = keys[lo];
+        bool before = lo > 0 && keys[lo - 1] == cur;
+        for (int64_t i = lo; i < hi; ++i) {
+            const int key = keys[i];
+            if (key != cur) {
+                emit_run<NQ>(P.G, P.Rp, P.rowoff[P.n_mode], cur, acc, col, before, false, (int)c, ckey, cvec);
+#pragma unroll
+                for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
+                cur = key;
+                before = false;
+            }
+            const int s = ids[i];
+            const float y = P.Yval[s];
+            float prod[COLS];
+#pragma unroll
+            for (int v = 0; v < COLS; ++v) prod[v] = y;
+            for (int k = 0; k < P.d; ++k) {
+                if (k == P.n_mode) continue;
+                float a[COLS];
+                load_cols<TF, NQ>(F, (P.rowoff[k] + P.Ycoord[(int64_t)s * P.d + k]) * P.Rp, col, a);
+#pragma unroll
+                for (int v = 0; v < COLS; ++v) prod[v] *= a[v];
+            }
+#pragma unroll
+            for (int v = 0; v < COLS; ++v) acc[v] += prod[v];
+        }
+        const bool after = hi < n && keys[hi] == cur;
+        emit_run<NQ>(P.G, P.Rp, P.rowoff[P.n_mode], cur, acc, col, before, after, (int)c, ckey, cvec);
+    }
+}
+
+// Levels 2+: sorted (key, partial vector) list -> G rows and edge carries.
+template <int COLS>
+__global__ void __launch_bounds__(kT) k_seg_vectors(const SegSpec P, const int32_t *__restrict__ keys,
+                                                    const float *__restrict__ vecs, int64_t n, int32_t *ckey,
+                                                    float *cvec) {
+    constexpr int NQ = COLS / 4;
+    const int lane = threadIdx.x & 31;
+    const int L = 1 << P.log2L;
+    const int glane = lane & (L - 1);
+    const int64_t group = ((int64_t)blockIdx.x * kT + threadIdx.x) >> P.log2L;
+    const int64_t ngroups = ((int64_t)gridDim.x * kT) >> P.log2L;
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    int col[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) col[q] = q * (P.Rp >> 1) + 4 * glane;
+    for (int64_t c = group; c < nchunks; c += ngroups) {
+        const int64_t lo = c * kChunk, hi = lo + kChunk < n ? lo + kChunk : n;
+        float acc[COLS];
+#pragma unroll
+        for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
+        int cur = keys[lo];
+        bool before = lo > 0 && keys[lo - 1] == cur;
+        for (int64_t i = lo; i < hi; ++i) {
+            const int key = keys[i];
+            if (key != cur) {
+                emit_run<NQ>(P.G, P.Rp, P.rowoff[P.n_mode], cur, acc, col, before, false, (int)c, ckey, cvec);
+#pragma unroll
+                for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
+                cur = key;
+                before = false;
+            }
+            const float *vv = vecs + i * P.Rp;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const float4 t = *reinterpret_cast<const float4 *>(vv + col[q]);
+                acc[4 * q] += t.x;
+                acc[4 * q + 1] += t.y;
+                acc[4 * q + 2] += t.z;
+                acc[4 * q + 3] += t.w;
+            }
+        }
+        const bool after = hi < n && keys[hi] == cur;
+        emit_run<NQ>(P.G, P.Rp, P.rowoff[P.n_mode], cur, acc, col, before, after, (int)c, ckey, cvec);
+    }
+}
+
+__global__ void k_fill_int(int32_t *a, int64_t n, int32_t v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+// flag[i] = 1 if carry slot i is used.
+__global__ void k_carry_flags(const int32_t *ckey, int64_t n, int32_t *flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = ckey[i] >= 0 ? 1 : 0;
+}
+
+// Order-preserving compaction of the used carry slots.
+__global__ void k_carry_compact(const int32_t *ckey, const float *cvec, int64_t n, const int32_t *pos, int Rp,
+                                int32_t *okey, float *ovec) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * Rp;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / Rp;
+        const int c = (int)(e % Rp);
+        if (ckey[i] < 0) continue;
+        const int64_t o = pos[i];
+        ovec[o * Rp + c] = cvec[i * Rp + c];
+        if (c == 0) okey[o] = ckey[i];
+    }
+}
+
+int grid_for(int64_t items, int per_block) {
+    int64_t b = (items + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > 65535) b = 65535;
+    return (int)b;
+}
+
+}  // namespace
+
+// Scratch for the deterministic variant, grown on demand.
+static gcp_status det_scratch(gcp_ctx *c, int64_t S, size_t *offs) {
+    const int64_t ntiles = (S + kTile - 1) / kTile;
+    const int64_t nchunk = (S + kChunk - 1) / kChunk + 1;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += (bytes + 255) & ~(size_t)255;
+        return at;
+    };
+    offs[0] = take((size_t)S * c->d * 4);           // Ycoord
+    offs[1] = take((size_t)S * 4);                  // Yval
+    offs[2] = take((size_t)S * 4);                  // keys A
+    offs[3] = take((size_t)S * 4);                  // vals A
+    offs[4] = take((size_t)S * 4);                  // keys B
+    offs[5] = take((size_t)S * 4);                  // vals B
+    offs[6] = take((size_t)256 * ntiles * 4);       // digit histograms / offsets
+    offs[7] = take((size_t)2 * nchunk * 4);         // carry keys (level in)
+    offs[8] = take((size_t)2 * nchunk * c->Rp * 4); // carry vectors (level in)
+    offs[9] = take((size_t)2 * nchunk * 4);         // carry keys (level out)
+    offs[10] = take((size_t)2 * nchunk * c->Rp * 4);
+    offs[11] = take((size_t)2 * nchunk * 4);        // compaction positions
+    offs[12] = take((size_t)2 * nchunk * 4);        // compacted keys
+    offs[13] = take((size_t)2 * nchunk * c->Rp * 4);
+    offs[14] = take(16);                            // list length
+    if (o > c->det_scratch_bytes) {
+        cudaFree(c->det_scratch);
+        c->det_scratch = nullptr;
+        c->det_scratch_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->det_scratch, o);
+        if (e != cudaSuccess) {
+            c->err = std::string("allocating deterministic MTTKRP scratch: ") + cudaGetErrorString(e);
+            return e == cudaErrorMemoryAllocation ? GCP_ERR_OOM : GCP_ERR_CUDA;
+        }
+        c->det_scratch_bytes = o;
+    }
+    return GCP_OK;
+}
+
+#define DET_CUDA(call)                                                           \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) {                                                 \
+            c->err = std::string(#call) + ": " + cudaGetErrorString(e_);         \
+            return GCP_ERR_CUDA;                                                 \
+        }                                                                        \
+    } while (0)
+
+template <typename TF>
+static void launch_seg_samples(const SegSpec &P, int cols, int grid, const int32_t *keys, const int32_t *ids,
+                               int64_t n, int32_t *ckey, float *cvec, cudaStream_t st) {
+    if (cols == 8)
+        k_seg_samples<TF, 8><<<grid, kT, 0, st>>>(P, keys, ids, n, ckey, cvec);
+    else
+        k_seg_samples<TF, 4><<<grid, kT, 0, st>>>(P, keys, ids, n, ckey, cvec);
+}
+
+gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
+    const int64_t S = f0.s.p + f0.s.q;
+    size_t offs[15];
+    gcp_status s = det_scratch(c, S > 0 ? S : 1, offs);
+    if (s) return s;
+    char *base = static_cast<char *>(c->det_scratch);
+    int32_t *Ycoord = reinterpret_cast<int32_t *>(base + offs[0]);
+    float *Yval = reinterpret_cast<float *>(base + offs[1]);
+    int32_t *kA = reinterpret_cast<int32_t *>(base + offs[2]), *vA = reinterpret_cast<int32_t *>(base + offs[3]);
+    int32_t *kB = reinterpret_cast<int32_t *>(base + offs[4]), *vB = reinterpret_cast<int32_t *>(base + offs[5]);
+    int32_t *hist = reinterpret_cast<int32_t *>(base + offs[6]);
+    int32_t *ckey_in = reinterpret_cast<int32_t *>(base + offs[7]);
+    float *cvec_in = reinterpret_cast<float *>(base + offs[8]);
+    int32_t *ckey_out = reinterpret_cast<int32_t *>(base + offs[9]);
+    float *cvec_out = reinterpret_cast<float *>(base + offs[10]);
+    int32_t *cpos = reinterpret_cast<int32_t *>(base + offs[11]);
+    int32_t *lkey = reinterpret_cast<int32_t *>(base + offs[12]);
+    float *lvec = reinterpret_cast<float *>(base + offs[13]);
+    int32_t *dlen = reinterpret_cast<int32_t *>(base + offs[14]);
+    cudaStream_t st = c->st;
+
+    // 1. loss partials and the materialised gradient tensor
+    gcpk::FusedSpec f = f0;
+    f.G = nullptr;
+    f.Ycoord = Ycoord;
+    f.Yval = Yval;
+    DET_CUDA(gcpk::launch_fused(f, c->Abf != nullptr, c->cols, c->max_blocks, st, blocks));
+    if (S == 0) return GCP_OK;
+
+    const int64_t ntiles = (S + kTile - 1) / kTile;
+    SegSpec P{};
+    P.d = c->d;
+    P.Rp = c->Rp;
+    P.cols = c->cols;
+    P.log2L = c->log2L;
+    for (int k = 0; k < c->d; ++k) P.rowoff[k] = (int)c->rowoff[k];
+    P.F = f0.F;
+    P.Ycoord = Ycoord;
+    P.Yval = Yval;
+    P.G = c->G;
+    const int lanes = 1 << c->log2L;
+    for (int n = 0; n < c->d; ++n) {
+        P.n_mode = n;
+        // 2. stable LSD radix sort of sample ids by row i_n
+        int bits = 1;
+        while ((1ll << bits) < c->dims[n]) ++bits;
+        const int32_t *kin = Ycoord + n;
+        int kstride = c->d;
+        const int32_t *vin = nullptr;
+        int32_t *kout = kA, *vout = vA;
+        for (int shift = 0; shift < bits; shift += 8) {
+            k_radix_hist<<<(int)ntiles, kT, 0, st>>>(kin, kstride, S, shift, hist, (int)ntiles);
+            k_scan_exclusive<<<1, kT, 0, st>>>(hist, 256 * ntiles, nullptr);
+            k_radix_scatter<<<(int)ntiles, kT, 0, st>>>(kin, kstride, vin, S, shift, hist, (int)ntiles, kout, vout);
+            DET_CUDA(cudaGetLastError());
+            kin = kout;
+            vin = vout;
+            kstride = 1;
+            kout = (kout == kA) ? kB : kA;
+            vout = (vout == vA) ? vB : vA;
+        }
+        // 3. chunked segmented reduction, level 1 over samples
+        int64_t nch = (S + kChunk - 1) / kChunk;
+        const int grid = grid_for(nch * lanes, kT);
+        k_fill_int<<<grid_for(2 * nch, kT), kT, 0, st>>>(ckey_out, 2 * nch, -1);
+        if (c->Abf)
+            launch_seg_samples<__nv_bfloat16>(P, c->cols, grid, kin, vin, S, ckey_out, cvec_out, st);
+        else
+            launch_seg_samples<float>(P, c->cols, grid, kin, vin, S, ckey_out, cvec_out, st);
+        DET_CUDA(cudaGetLastError());
+        // levels 2+: compact the carries and reduce them again
+        int64_t nslots = 2 * nch;
+        while (nch > 1) {
+            k_carry_flags<<<grid_for(nslots, kT), kT, 0, st>>>(ckey_out, nslots, cpos);
+            k_scan_exclusive<<<1, kT, 0, st>>>(cpos, nslots, dlen);
+            k_carry_compact<<<grid_for(nslots * c->Rp, kT), kT, 0, st>>>(ckey_out, cvec_out, nslots, cpos, c->Rp,
+                                                                         lkey, lvec);
+            int32_t len = 0;
+            DET_CUDA(cudaMemcpyAsync(&len, dlen, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            DET_CUDA(cudaStreamSynchronize(st));
+            if (len == 0) break;
+            nch = (len + kChunk - 1) / kChunk;
+            nslots = 2 * nch;
+            std::swap(ckey_in, ckey_out);
+            std::swap(cvec_in, cvec_out);
+            k_fill_int<<<grid_for(nslots, kT), kT, 0, st>>>(ckey_out, nslots, -1);
+            if (c->cols == 8)
+                k_seg_vectors<8><<<grid_for(nch * lanes, kT), kT, 0, st>>>(P, lkey, lvec, len, ckey_out, cvec_out);
+            else
+                k_seg_vectors<4><<<grid_for(nch * lanes, kT), kT, 0, st>>>(P, lkey, lvec, len, ckey_out, cvec_out);
+            DET_CUDA(cudaGetLastError());
+        }
+    }
+    return GCP_OK;
 }

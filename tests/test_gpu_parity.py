@@ -331,3 +331,37 @@ def test_zipf_count_full_size(env, zipf_full, dtype, tol):
         assert abs(Lg - Lf) <= TOL_BF16 * abs(Lf)
         assert rel_err(Gg, np.concatenate([g.ravel() for g in Gf])) <= TOL_BF16
     ctx.close()
+
+
+# --------------------------------------------------- deterministic MTTKRP
+@pytest.mark.parametrize("dims,R,loss,dtype,p,q", [
+    ([2000, 1500, 1000, 200], 32, "poisson", "fp32", 20000, 20011),  # Zipf heads span many chunks
+    ([60, 50, 40], 64, "bernoulli", "fp32", 3000, 2999),              # 8 columns per lane
+    ([23, 17, 11, 7, 5], 16, "gamma", "bf16", 1500, 1001),
+    ([5000, 3], 8, "gaussian", "fp32", 1 << 18, 1 << 18),             # rows of ~175k samples: 3 levels
+])
+def test_deterministic_mttkrp_parity_and_bit_stability(env, dims, R, loss, dtype, p, q):
+    gcp, torch = env
+    if dims[0] == 2000:
+        w = synth.workload_zipf_count(scale=0.01)
+        coords, vals, factors = w["coords"], w["vals"], w["factors"]
+    else:
+        coords, vals, factors = problem(dims, min(3000, int(np.prod(dims)) // 3), R, loss, 700 + len(dims))
+    det = gcp.gcp_create(dims, coords, vals, R, loss, dtype=dtype, seed=21, mttkrp="deterministic")
+    det.set_factors(factors)
+    L1, G1 = gpu_grad(gcp, torch, det, 6, p, q)
+    L2, G2 = gpu_grad(gcp, torch, det, 6, p, q)
+    assert L1 == L2 and np.array_equal(G1.view(np.uint32), G2.view(np.uint32))  # bit-identical
+    fac = [bf16_round(a) for a in factors] if dtype == "bf16" else factors
+    idx, x, wt, _ = oracle.stratified_samples(21, 6, p, q, dims, coords, vals)
+    Lo, Go = oracle.sampled_loss_grad(dims, fac, loss, idx, x, wt)
+    assert abs(L1 - Lo) <= TOL_FP32 * abs(Lo)
+    for n, (a, b) in enumerate(zip(split(G1, dims, R), Go)):
+        assert rel_err(a, b) <= TOL_FP32, (n, rel_err(a, b))
+    atom = gcp.gcp_create(dims, coords, vals, R, loss, dtype=dtype, seed=21)
+    atom.set_factors(factors)
+    La, Ga = gpu_grad(gcp, torch, atom, 6, p, q)
+    assert La == L1  # the loss reduction is fixed-order in both variants
+    assert rel_err(G1, Ga) <= TOL_FP32
+    det.close()
+    atom.close()
