@@ -329,7 +329,8 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": base,
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(A_host.numel() * 4),
                     "d2h_bytes_per_step": int(G_host.numel() * 4 + 8)},
-            "gpu_launches": 3 * args.steps, "clocks": clocks,
+            # per step: k_fused, k_fold_replicas, k_finish_loss, k_adam (plus one G memset)
+            "gpu_launches": 4 * args.steps, "clocks": clocks,
             "variants": {"bf16_factors": {"value": bf16_value, "unit": "samples/s",
                                           "kernel_ms_per_launch": kms_bf / max(1, nl_bf),
                                           "achieved_gbs": bps_bf * S / (kms_bf / 1e3 / max(1, nl_bf)) / 1e9}}}
