@@ -241,6 +241,42 @@ gcp_status gcp_fit(gcp_ctx *ctx, const gcp_fit_params *prm, gcp_fit_report *repo
 gcp_status gcp_profile(gcp_ctx *ctx, int32_t enable);
 gcp_status gcp_profile_read(gcp_ctx *ctx, double *kernel_ms, int64_t *launches);
 
+/* ---- Batched independent subproblems (the client shards of the federated
+ * schemes, Alg. 3 and Alg. 4, simulated on one GPU) ----
+ * A batch advances many contexts ("clients") together: one local step runs,
+ * for every client c, the sampled gradient of p[c] nonzero and q[c] zero
+ * samples followed by its own Adam update, with one multi-client launch per
+ * kernel; tau local steps are captured once in a CUDA graph and replayed. */
+
+/* Create a batch over nclients existing sparse contexts (kept by the caller,
+ * who must not destroy them before the batch).  They must share order, rank,
+ * loss, factor dtype, device and stream, use the atomic MTTKRP and
+ * stratified or semi-stratified sampling.  p, q (host, nclients): samples per
+ * local step of each client, p[c] + q[c] < 2^31.  The batch works on its own
+ * stream, ordered after and before the clients' stream with events. */
+gcp_status gcp_batch_create(int32_t nclients, gcp_ctx *const *clients, const int64_t *p, const int64_t *q,
+                            gcp_batch **out);
+void gcp_batch_destroy(gcp_batch *batch);
+const char *gcp_batch_last_error(const gcp_batch *batch);
+
+/* Tuning knobs of the multi-client fused kernel: factor columns per lane (4
+ * or 8; 0 = the clients' choice) and the number of thread blocks of the
+ * persistent grid (0 = all that fit on the GPU at once).  A change rebuilds
+ * the graph at the next gcp_batch_local_steps. */
+gcp_status gcp_batch_tune(gcp_batch *batch, int32_t lane_cols, int32_t blocks);
+
+/* tau local steps of every client: step k (0-based) samples iteration
+ * iter0 + k and applies Adam step t0 + k + 1 (Alg. 1) with prm.  Each client
+ * ends with the same state as tau rounds of gcp_grad + gcp_adam_step on its
+ * own context, up to the summation order of the atomic MTTKRP.
+ * Asynchronous on the clients' stream. */
+gcp_status gcp_batch_local_steps(gcp_batch *batch, int32_t tau, const gcp_adam_params *prm, uint64_t iter0,
+                                 int64_t t0);
+
+/* Sampled loss of every client's last local step (host, nclients doubles).
+ * Synchronises; returns any pending device error of a client. */
+gcp_status gcp_batch_losses(gcp_batch *batch, double *loss_out);
+
 /* Sampled loss and gradient of a caller-supplied sample list, allocating
  * nothing.  The paper has no counterpart: it exists for callers that cannot
  * allocate device memory -- code that runs under a device-memory budget

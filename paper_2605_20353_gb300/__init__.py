@@ -91,6 +91,12 @@ SIGNATURES = {
     "gcp_fit": (_i32, [_vp, ctypes.POINTER(gcp_fit_params), ctypes.POINTER(gcp_fit_report)]),
     "gcp_profile": (_i32, [_vp, _i32]),
     "gcp_profile_read": (_i32, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_i64)]),
+    "gcp_batch_create": (_i32, [_i32, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "gcp_batch_destroy": (None, [_vp]),
+    "gcp_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "gcp_batch_tune": (_i32, [_vp, _i32, _i32]),
+    "gcp_batch_local_steps": (_i32, [_vp, _i32, ctypes.POINTER(gcp_adam_params), _u64, _i64]),
+    "gcp_batch_losses": (_i32, [_vp, _vp]),
     "gcp_grad_samples_noalloc": (_i32, [_i32, _vp, _i32, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
@@ -321,6 +327,52 @@ def gcp_create_dense(dims, X, rank, loss, dtype="fp32", seed=0, stream=None, lan
     _check(lib.gcp_create_dense(len(d), d.ctypes.data, _ptr(X), rank, LOSSES[loss], ctypes.byref(opt),
                                 ctypes.byref(h)), None)
     return GcpContext(h.value, d, rank, loss, dtype, stream)
+
+
+class GcpBatch:
+    """Many client contexts advanced together (one multi-client launch per
+    kernel, tau local steps in one CUDA graph)."""
+
+    def __init__(self, clients, p, q):
+        lib = load()
+        self.clients = list(clients)  # keep the contexts alive
+        arr = (ctypes.c_void_p * len(self.clients))(*[c.handle for c in self.clients])
+        pp = np.ascontiguousarray(p, dtype=np.int64)
+        qq = np.ascontiguousarray(q, dtype=np.int64)
+        h = ctypes.c_void_p()
+        rc = lib.gcp_batch_create(len(self.clients), ctypes.cast(arr, ctypes.c_void_p), pp.ctypes.data,
+                                  qq.ctypes.data, ctypes.byref(h))
+        if rc != GCP_OK:
+            raise GcpError(rc, lib.gcp_batch_last_error(None).decode())
+        self.handle = h.value
+        self.p, self.q = pp, qq
+
+    def _check(self, rc):
+        if rc != GCP_OK:
+            raise GcpError(rc, load().gcp_batch_last_error(self.handle).decode())
+
+    def tune(self, lane_cols=0, blocks=0):
+        self._check(load().gcp_batch_tune(self.handle, lane_cols, blocks))
+
+    def local_steps(self, tau, adam: AdamParams, iter0, t0):
+        c = adam.c()
+        self._check(load().gcp_batch_local_steps(self.handle, tau, ctypes.byref(c), iter0, t0))
+
+    def losses(self):
+        out = np.zeros(len(self.clients), dtype=np.float64)
+        self._check(load().gcp_batch_losses(self.handle, out.ctypes.data))
+        return out
+
+    def close(self):
+        if self.handle:
+            load().gcp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gcp_grad_samples_noalloc(dims, rank, loss, idx, x, w, A, G, loss_out, stream=None):

@@ -248,9 +248,12 @@ gcp_status check_counts(gcp_ctx *c, int64_t p, int64_t q) {
 }
 
 // One fused pass: loss always, gradient into c->G when `grad`.
-gcp_status run_fused(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad, const float *dscale) {
-    gcp_status s = check_counts(c, p, q);
-    if (s) return s;
+}  // namespace
+
+// The fused-pass parameters of one sample set of a context (also used for
+// each client of a batch).
+gcpk::FusedSpec gcpk_make_spec(const gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad,
+                               const float *dscale, double *w_nz_out, double *w_z_out) {
     double w_nz, w_z;
     weights(c, p, q, w_nz, w_z);
     gcpk::FusedSpec f{};
@@ -268,6 +271,20 @@ gcp_status run_fused(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad,
     for (int k = 0; k < c->d; ++k) f.small_base[k] = c->small_base[k];
     f.Grep = c->Grep;
     f.Htot = c->Htot;
+    if (w_nz_out) *w_nz_out = w_nz;
+    if (w_z_out) *w_z_out = w_z;
+    return f;
+}
+
+gcp_status gcpk_check_counts(gcp_ctx *c, int64_t p, int64_t q) { return check_counts(c, p, q); }
+
+namespace {
+
+gcp_status run_fused(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad, const float *dscale) {
+    gcp_status s = check_counts(c, p, q);
+    if (s) return s;
+    double w_nz, w_z;
+    gcpk::FusedSpec f = gcpk_make_spec(c, iter, p, q, grad, dscale, &w_nz, &w_z);
     if (grad) GCP_CUDA(c, cudaMemsetAsync(c->G, 0, (size_t)c->total_rows * c->Rp * 4, c->st));
     int blocks = 0;
     cudaEvent_t stop = nullptr;

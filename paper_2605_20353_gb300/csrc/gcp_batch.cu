@@ -1,0 +1,706 @@
+// gcp_batch.cu -- many independent GCP subproblems advanced together.
+//
+// The federated schemes of the paper (LocalSGD, Alg. 3; GCP-FedAdam, Alg. 4)
+// run many local GCP-Adam steps on independent shards.  Here the shards
+// ("clients") live on one GPU, each with its own tensor, model and Adam
+// state (a gcp_ctx).  One local step of every client is one launch of each
+// of: zero the gradients, the multi-client fused sampled gradient
+// (sampling, model, loss, all-mode MTTKRP; Sec. 3.1.1-3.1.2), fold the hot-row
+// replicas, finish the per-client losses, the multi-client Adam update
+// (Alg. 1), advance the step counters.  tau local steps are captured once in
+// a CUDA graph and replayed; the iteration number and Adam step live in
+// device memory so every replay continues where the last one stopped.
+//
+// The fused kernel is persistent: warps walk a global list of 32-sample
+// tiles; client c owns tiles tile_start[c] .. tile_start[c+1]-1, so a tile
+// never mixes clients, and a warp stages the client's parameters in shared
+// memory next to the tile's samples (double-buffered like them).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gcp_device.cuh"
+#include "gcp_internal.h"
+
+using namespace gcpdev;
+
+namespace gcpb {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kSpecWords = (int)((sizeof(gcpk::FusedSpec) + 15) / 16);  // 16-byte words of a FusedSpec
+
+// Per-client state used by the zero / fold / finish / Adam kernels.
+struct ClientAux {
+    float *A, *B, *C, *G, *Grep;
+    void *Abf;
+    const int *hot_row;
+    int Htot;
+    int64_t nparam;  // total_rows * Rp
+    int R, Rp;
+    double w_nz, w_z;
+    int tile0, ntiles;
+};
+
+template <int D>
+__device__ __forceinline__ void draw_tuple_b(const gcpk::SampleSpec &S, uint64_t stream, uint64_t j, uint64_t sub0,
+                                             int32_t (&idx)[D]) {
+#pragma unroll
+    for (int b = 0; 4 * b < D; ++b) {
+        const U64x4 w = philox4x64_10(j, sub0 + (uint64_t)b, S.iter, 0, S.seed, stream);
+#pragma unroll
+        for (int k = 4 * b; k < D && k < 4 * b + 4; ++k)
+            idx[k] = (int32_t)map_range(w.v[k - 4 * b], (uint64_t)S.dims[k]);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ uint64_t linear_b(const gcpk::SampleSpec &S, const int32_t (&idx)[D]) {
+    uint64_t L = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) L += (uint64_t)idx[k] * S.stride[k];
+    return L;
+}
+
+__device__ __forceinline__ int client_of(const int *__restrict__ tile_start, int nclients, int tile) {
+    int lo = 0, hi = nclients;  // last c with tile_start[c] <= tile
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(tile_start + mid) <= tile)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Multi-client fused sampled gradient.  Each client's FusedSpec (stored as
+// kSpecWords 16-byte words) gives its
+// tensor, model, gradient and weights; the iteration number is step[0].
+// Per tile, the FP32 loss sums (nonzero, zero) go to tile_loss[tile].
+template <int D, typename TF, int COLS>
+__global__ void __launch_bounds__(kThreads) k_batch_fused(const int4 *__restrict__ specs,
+                                                         const int *__restrict__ tile_start, int nclients,
+                                                         int total_tiles, int log2L, int Rp,
+                                                         const uint64_t *__restrict__ step, float2 *tile_loss) {
+    constexpr int SW = gcpk::rec_words_for(D);
+    constexpr int NQ = COLS / 4;
+    __shared__ __align__(16) int32_t s_slot[2][kWarps][32][SW];
+    __shared__ __align__(16) uint64_t s_bkt[2][kWarps][32][4];
+    __shared__ __align__(16) int4 s_spec[2][kWarps][kSpecWords];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int L = 1 << log2L;
+    const int glane = lane & (L - 1);
+    const int grp = lane >> log2L;
+    const int ngrp = 32 >> log2L;
+    const unsigned gmask = (L == 32) ? 0xFFFFFFFFu : (((1u << L) - 1u) << (grp * L));
+    int col[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) col[q] = q * (Rp >> 1) + 4 * glane;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t iter = __ldg(step);
+    int cur_client[2] = {-1, -1};
+
+    auto spec_of = [&](int st) -> const gcpk::FusedSpec & {
+        return *reinterpret_cast<const gcpk::FusedSpec *>(&s_spec[st][warp][0]);
+    };
+    // Stage the parameters of the client owning `tile` (whole warp).
+    auto stage_spec = [&](int tile, int st) -> int {
+        const int c = client_of(tile_start, nclients, tile);
+        if (c != cur_client[st]) {
+            const int4 *src = specs + (size_t)c * kSpecWords;  // specs padded to kSpecWords words
+            for (int i = lane; i < kSpecWords; i += 32) s_spec[st][warp][i] = __ldg(src + i);
+            __syncwarp();
+            if (lane == 0) reinterpret_cast<gcpk::FusedSpec *>(&s_spec[st][warp][0])->s.iter = iter;
+            __syncwarp();
+            cur_client[st] = c;
+        }
+        return c;
+    };
+
+    auto issue = [&](int tile, int st) -> uint64_t {
+        if (tile >= total_tiles) return kEmpty;
+        const int c = stage_spec(tile, st);
+        const gcpk::FusedSpec &P = spec_of(st);
+        const int p = (int)P.s.p, S = (int)(P.s.p + P.s.q);
+        const int s = ((tile - __ldg(tile_start + c)) << 5) + lane;
+        int32_t *slot = s_slot[st][warp][lane];
+        if (s >= S) return kEmpty;
+        if (s < p) {
+            const U64x4 w = philox4x64_10((uint64_t)s, 0, P.s.iter, 0, P.s.seed, kStreamNonzero);
+            const int32_t *rec = P.s.rec + map_range(w.v[0], (uint64_t)P.s.nnz) * SW;
+#pragma unroll
+            for (int v = 0; v < SW / 4; ++v) cp_async16(slot + 4 * v, rec + 4 * v);
+            return kEmpty;
+        }
+        const bool semi = P.s.sampling == GCP_SAMPLING_SEMI_STRATIFIED;
+        int32_t idx[D];
+        draw_tuple_b<D>(P.s, semi ? kStreamSemiZero : kStreamZero, (uint64_t)(s - p), 0, idx);
+#pragma unroll
+        for (int k = 0; k < D; ++k) slot[k] = idx[k];
+        slot[D] = 0;
+        if (semi) return kEmpty;
+        const uint64_t key = linear_b<D>(P.s, idx);
+        const uint64_t *b = P.s.hkeys + 4 * (mix64(key) & P.s.hbmask);
+        cp_async16(&s_bkt[st][warp][lane][0], b);
+        cp_async16(&s_bkt[st][warp][lane][2], b + 2);
+        return key;
+    };
+
+    auto finish = [&](int tile, int st, uint64_t key) -> bool {
+        const gcpk::FusedSpec &P = spec_of(st);
+        const int p = (int)P.s.p, S = (int)(P.s.p + P.s.q);
+        const int s = ((tile - __ldg(tile_start + cur_client[st])) << 5) + lane;
+        if (s >= S) return false;
+        if (key == kEmpty) return true;
+        const ulonglong2 lo = *reinterpret_cast<const ulonglong2 *>(&s_bkt[st][warp][lane][0]);
+        const ulonglong2 hi = *reinterpret_cast<const ulonglong2 *>(&s_bkt[st][warp][lane][2]);
+        int h = bucket_decide(lo, hi, key);
+        if (h == 2)
+            h = hash_contains_from(P.s.hkeys, P.s.hbmask, key, ((mix64(key) & P.s.hbmask) + 1) & P.s.hbmask, 1);
+        if (h == 0) return true;
+        int32_t *slot = s_slot[st][warp][lane];
+        const uint64_t j = (uint64_t)(s - p);
+        for (int a = 1; h == 1 && a < P.s.max_attempts; ++a) {
+            int32_t idx[D];
+            draw_tuple_b<D>(P.s, kStreamZero, j, 4 * (uint64_t)a, idx);
+            h = hash_contains(P.s.hkeys, P.s.hbmask, linear_b<D>(P.s, idx));
+            if (h == 0) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) slot[k] = idx[k];
+                return true;
+            }
+        }
+        atomicOr(P.s.status, h < 0 ? kErrHashFull : kErrExhausted);
+        return false;
+    };
+
+    int tile = warp0;
+    uint64_t key_next = issue(tile, 0);
+    cp_async_commit();
+    for (int st = 0; tile < total_tiles; tile += nwarps, st ^= 1) {
+        const uint64_t key = key_next;
+        __syncwarp();
+        key_next = issue(tile + nwarps, st ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        const bool ok = finish(tile, st, key);
+        const unsigned okmask = __ballot_sync(0xFFFFFFFFu, ok);
+        __syncwarp();
+
+        const gcpk::FusedSpec &P = spec_of(st);
+        const TF *__restrict__ F = static_cast<const TF *>(P.F);
+        const int p = (int)P.s.p;
+        const int tbase = (tile - __ldg(tile_start + cur_client[st])) << 5;
+        const bool semi = P.s.sampling == GCP_SAMPLING_SEMI_STRATIFIED;
+        float *const grep = P.Grep ? P.Grep + (size_t)(warp0 & (gcpk::kReplicas - 1)) * P.Htot * Rp : nullptr;
+        float tf_nz = 0.0f, tf_z = 0.0f;
+        for (int it = 0; it < L; ++it) {
+            const int src = it * ngrp + grp;
+            if (!((okmask >> src) & 1u)) continue;
+            const int32_t *slot = s_slot[st][warp][src];
+            int32_t ii[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) ii[k] = slot[k];
+            const float xs = __int_as_float(slot[D]);
+            const bool is_nz = (tbase + src) < p;
+            int off[D];
+            float a[D][COLS];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                off[k] = (P.rowoff[k] + ii[k]) * Rp;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) Quad<TF>::load(F + off[k] + col[q], a[k] + 4 * q);
+            }
+            float suf[D][COLS];
+#pragma unroll
+            for (int v = 0; v < COLS; ++v) suf[D - 1][v] = 1.0f;
+#pragma unroll
+            for (int k = D - 2; k >= 0; --k)
+#pragma unroll
+                for (int v = 0; v < COLS; ++v) suf[k][v] = suf[k + 1][v] * a[k + 1][v];
+            float m = 0.0f;
+#pragma unroll
+            for (int v = 0; v < COLS; ++v) m = fmaf(a[0][v], suf[0][v], m);
+            for (int o = L >> 1; o > 0; o >>= 1) m += __shfl_xor_sync(gmask, m, o);
+            float f, df;
+            loss_eval(P.loss, xs, m, f, df);
+            if (semi && is_nz) {
+                float f0, df0;
+                loss_eval(P.loss, 0.0f, m, f0, df0);
+                f -= f0;
+                df -= df0;
+            }
+            if (is_nz)
+                tf_nz += f;
+            else
+                tf_z += f;
+            const float y = (is_nz ? P.w_nz : P.w_z) * df;
+            float pre[COLS];
+#pragma unroll
+            for (int v = 0; v < COLS; ++v) pre[v] = y;
+#pragma unroll
+            for (int n = 0; n < D; ++n) {
+                unsigned hs;
+                if (is_nz)
+                    hs = ((unsigned)slot[D + 1 + n / 2] >> (16 * (n & 1))) & 0xFFFFu;
+                else
+                    hs = P.small_base[n] >= 0 ? (unsigned)(P.small_base[n] + ii[n]) : gcpk::kNoSlot;
+                float *g = hs != gcpk::kNoSlot ? grep + (int)hs * Rp : P.G + off[n];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+                    red_add_v4(g + col[q], pre[4 * q] * suf[n][4 * q], pre[4 * q + 1] * suf[n][4 * q + 1],
+                               pre[4 * q + 2] * suf[n][4 * q + 2], pre[4 * q + 3] * suf[n][4 * q + 3]);
+#pragma unroll
+                for (int v = 0; v < COLS; ++v) pre[v] *= a[n][v];
+            }
+        }
+        // tile loss sums: one value per group leader, reduced over the warp
+        if (glane != 0) tf_nz = tf_z = 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tf_nz += __shfl_xor_sync(0xFFFFFFFFu, tf_nz, o);
+            tf_z += __shfl_xor_sync(0xFFFFFFFFu, tf_z, o);
+        }
+        if (lane == 0) tile_loss[tile] = make_float2(tf_nz, tf_z);
+    }
+    cp_async_wait<0>();
+}
+
+// ------------------------------------------------- per-client small kernels
+// grid.y = client; blocks of grid.x stride over that client's elements.
+__global__ void k_batch_zero(const ClientAux *__restrict__ aux) {
+    const ClientAux &a = aux[blockIdx.y];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.nparam; e += (int64_t)gridDim.x * blockDim.x)
+        a.G[e] = 0.0f;
+}
+
+// G(hot row) += sum of the replicas (all loads first), replicas cleared.
+__global__ void k_batch_fold(const ClientAux *__restrict__ aux) {
+    const ClientAux &a = aux[blockIdx.y];
+    const int64_t n = (int64_t)a.Htot * a.Rp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        float v[gcpk::kReplicas];
+#pragma unroll
+        for (int r = 0; r < gcpk::kReplicas; ++r) v[r] = a.Grep[r * n + e];
+        float t = 0.0f;
+#pragma unroll
+        for (int r = 0; r < gcpk::kReplicas; ++r) t += v[r];
+#pragma unroll
+        for (int r = 0; r < gcpk::kReplicas; ++r) a.Grep[r * n + e] = 0.0f;
+        a.G[(int64_t)a.hot_row[e / a.Rp] * a.Rp + e % a.Rp] += t;
+    }
+}
+
+// One block per client: its tiles' loss sums in fixed order, weighted.
+__global__ void k_batch_finish(const ClientAux *__restrict__ aux, const float2 *__restrict__ tile_loss,
+                               double *client_loss) {
+    const ClientAux &a = aux[blockIdx.x];
+    __shared__ double sh[2][kThreads];
+    double nz = 0.0, z = 0.0;
+    for (int t = threadIdx.x; t < a.ntiles; t += kThreads) {
+        const float2 v = tile_loss[a.tile0 + t];
+        nz += v.x;
+        z += v.y;
+    }
+    sh[0][threadIdx.x] = nz;
+    sh[1][threadIdx.x] = z;
+    __syncthreads();
+    for (int h = kThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + h];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) client_loss[blockIdx.x] = a.w_nz * sh[0][0] + a.w_z * sh[1][0];
+}
+
+// Algorithm 1 for every client; t = step[1] + 1; hyperparameters in adam[5]
+// (lr, beta1, beta2, eps, lower).  Padded columns stay zero.
+__global__ void k_batch_adam(const ClientAux *__restrict__ aux, const double *__restrict__ adam,
+                             const uint64_t *__restrict__ step) {
+    const ClientAux &a = aux[blockIdx.y];
+    __shared__ float c[7];
+    if (threadIdx.x == 0) {
+        const double t = (double)(step[1] + 1);
+        c[0] = (float)adam[0];
+        c[1] = (float)adam[1];
+        c[2] = (float)adam[2];
+        c[3] = (float)(1.0 / (1.0 - pow(adam[1], t)));
+        c[4] = (float)(1.0 / (1.0 - pow(adam[2], t)));
+        c[5] = (float)adam[3];
+        c[6] = (float)adam[4];
+    }
+    __syncthreads();
+    __nv_bfloat16 *Abf = static_cast<__nv_bfloat16 *>(a.Abf);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.nparam; e += (int64_t)gridDim.x * blockDim.x) {
+        if ((int)(e % a.Rp) >= a.R) continue;
+        const float g = a.G[e];
+        const float b = c[1] * a.B[e] + (1.0f - c[1]) * g;
+        const float cc = c[2] * a.C[e] + (1.0f - c[2]) * g * g;
+        a.B[e] = b;
+        a.C[e] = cc;
+        const float x = fmaxf(a.A[e] - c[0] * ((b * c[3]) / sqrtf(cc * c[4] + c[5])), c[6]);
+        a.A[e] = x;
+        if (Abf) Abf[e] = __float2bfloat16_rn(x);
+    }
+}
+
+__global__ void k_batch_advance(uint64_t *step) {
+    step[0] += 1;
+    step[1] += 1;
+}
+
+template <int D>
+cudaError_t launch_fused_d(bool bf16, int cols, int blocks, const int4 *specs, const int *tile_start, int n,
+                           int total_tiles, int log2L, int Rp, const uint64_t *step, float2 *tile_loss,
+                           cudaStream_t st) {
+    if (bf16) {
+        if (cols == 8)
+            k_batch_fused<D, __nv_bfloat16, 8><<<blocks, kThreads, 0, st>>>(specs, tile_start, n, total_tiles, log2L,
+                                                                           Rp, step, tile_loss);
+        else
+            k_batch_fused<D, __nv_bfloat16, 4><<<blocks, kThreads, 0, st>>>(specs, tile_start, n, total_tiles, log2L,
+                                                                           Rp, step, tile_loss);
+    } else {
+        if (cols == 8)
+            k_batch_fused<D, float, 8><<<blocks, kThreads, 0, st>>>(specs, tile_start, n, total_tiles, log2L, Rp,
+                                                                   step, tile_loss);
+        else
+            k_batch_fused<D, float, 4><<<blocks, kThreads, 0, st>>>(specs, tile_start, n, total_tiles, log2L, Rp,
+                                                                   step, tile_loss);
+    }
+    return cudaGetLastError();
+}
+
+template <int D>
+int occupancy_d(bool bf16, int cols) {
+    int per_sm = 0;
+    if (bf16)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, cols == 8 ? k_batch_fused<D, __nv_bfloat16, 8> : k_batch_fused<D, __nv_bfloat16, 4>, kThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, cols == 8 ? k_batch_fused<D, float, 8> : k_batch_fused<D, float, 4>, kThreads, 0);
+    return per_sm < 1 ? 1 : per_sm;
+}
+
+}  // namespace gcpb
+
+// ======================================================================= host
+struct gcp_batch {
+    int n = 0, d = 0, R = 0, Rp = 0, loss = 0, device = 0;
+    bool bf16 = false;
+    std::vector<gcp_ctx *> clients;
+    std::vector<int64_t> p, q;
+    int total_tiles = 0;
+    int cols = 4, blocks = 0;        // tuning knobs: columns per lane, fused-kernel grid
+    int4 *specs = nullptr;           // n x kSpecWords
+    int *tile_start = nullptr;       // n + 1
+    gcpb::ClientAux *aux = nullptr;  // n
+    float2 *tile_loss = nullptr;     // total_tiles
+    double *client_loss = nullptr;   // n
+    uint64_t *step = nullptr;        // [0] iteration of the next gradient, [1] Adam steps done
+    double *adam = nullptr;          // lr, beta1, beta2, eps, lower
+    uint64_t *h_step = nullptr;      // pinned staging
+    double *h_adam = nullptr;
+    double *h_loss = nullptr;
+    int64_t max_param = 0, max_rep = 0;
+    cudaStream_t st = nullptr, user_st = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_tau = 0, graph_cols = 0, graph_blocks = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_create_err;
+
+gcp_status bfail(gcp_batch *b, gcp_status s, const std::string &m) {
+    if (b)
+        b->err = m;
+    else
+        g_batch_create_err = m;
+    return s;
+}
+
+#define BCUDA(b, call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? GCP_ERR_OOM : GCP_ERR_CUDA,        \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+void batch_free(gcp_batch *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->specs);
+    cudaFree(b->tile_start);
+    cudaFree(b->aux);
+    cudaFree(b->tile_loss);
+    cudaFree(b->client_loss);
+    cudaFree(b->step);
+    cudaFree(b->adam);
+    cudaFreeHost(b->h_step);
+    cudaFreeHost(b->h_adam);
+    cudaFreeHost(b->h_loss);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->st) cudaStreamDestroy(b->st);
+}
+
+int default_blocks(const gcp_batch *b, int cols) {
+    int per_sm = 1;
+    switch (b->d) {
+    case 2: per_sm = gcpb::occupancy_d<2>(b->bf16, cols); break;
+    case 3: per_sm = gcpb::occupancy_d<3>(b->bf16, cols); break;
+    case 4: per_sm = gcpb::occupancy_d<4>(b->bf16, cols); break;
+    case 5: per_sm = gcpb::occupancy_d<5>(b->bf16, cols); break;
+    case 6: per_sm = gcpb::occupancy_d<6>(b->bf16, cols); break;
+    case 7: per_sm = gcpb::occupancy_d<7>(b->bf16, cols); break;
+    default: per_sm = gcpb::occupancy_d<8>(b->bf16, cols); break;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    return per_sm * sms;
+}
+
+cudaError_t launch_batch_fused(const gcp_batch *b) {
+    const int log2L = [&] {
+        int l = 0;
+        while ((1 << l) * b->cols < b->Rp) ++l;
+        return l;
+    }();
+    switch (b->d) {
+#define GCPB_CASE(D)                                                                                              \
+    case D:                                                                                                       \
+        return gcpb::launch_fused_d<D>(b->bf16, b->cols, b->blocks, b->specs, b->tile_start, b->n, b->total_tiles, \
+                                       log2L, b->Rp, b->step, b->tile_loss, b->st);
+        GCPB_CASE(2)
+        GCPB_CASE(3)
+        GCPB_CASE(4)
+        GCPB_CASE(5)
+        GCPB_CASE(6)
+        GCPB_CASE(7)
+        GCPB_CASE(8)
+#undef GCPB_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// One local step of every client, enqueued on b->st (also used for capture).
+gcp_status enqueue_step(gcp_batch *b) {
+    const int nb = gcpb::kThreads;
+    const dim3 gp((unsigned)std::min<int64_t>(64, (b->max_param + nb - 1) / nb), (unsigned)b->n);
+    const dim3 gr((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (b->max_rep + nb - 1) / nb)), (unsigned)b->n);
+    gcpb::k_batch_zero<<<gp, nb, 0, b->st>>>(b->aux);
+    BCUDA(b, cudaGetLastError());
+    BCUDA(b, launch_batch_fused(b));
+    if (b->max_rep > 0) gcpb::k_batch_fold<<<gr, nb, 0, b->st>>>(b->aux);
+    gcpb::k_batch_finish<<<b->n, nb, 0, b->st>>>(b->aux, b->tile_loss, b->client_loss);
+    gcpb::k_batch_adam<<<gp, nb, 0, b->st>>>(b->aux, b->adam, b->step);
+    gcpb::k_batch_advance<<<1, 1, 0, b->st>>>(b->step);
+    BCUDA(b, cudaGetLastError());
+    return GCP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gcp_status gcp_batch_create(int32_t nclients, gcp_ctx *const *clients, const int64_t *p, const int64_t *q,
+                            gcp_batch **out) {
+    if (!out) return bfail(nullptr, GCP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nclients < 1 || !clients || !p || !q) return bfail(nullptr, GCP_ERR_ARG, "need nclients >= 1, clients, p, q");
+    const gcp_ctx *c0 = clients[0];
+    if (!c0) return bfail(nullptr, GCP_ERR_ARG, "NULL client");
+    int64_t tiles = 0;
+    for (int i = 0; i < nclients; ++i) {
+        const gcp_ctx *c = clients[i];
+        if (!c) return bfail(nullptr, GCP_ERR_ARG, "NULL client");
+        if (c->dense || c->opt.sampling == GCP_SAMPLING_UNIFORM)
+            return bfail(nullptr, GCP_ERR_ARG, "batched clients must be sparse tensors");
+        if (c->opt.mttkrp != GCP_MTTKRP_ATOMIC) return bfail(nullptr, GCP_ERR_ARG, "batched clients use the atomic MTTKRP");
+        if (c->d != c0->d || c->R != c0->R || c->Rp != c0->Rp || c->loss != c0->loss ||
+            (c->Abf != nullptr) != (c0->Abf != nullptr) || c->device != c0->device || c->st != c0->st)
+            return bfail(nullptr, GCP_ERR_ARG,
+                         "clients must share order, rank, loss, factor dtype, device and stream");
+        if (p[i] < 0 || q[i] < 0 || p[i] + q[i] >= ((int64_t)1 << 31))
+            return bfail(nullptr, GCP_ERR_ARG, "per-client sample counts must be >= 0 and sum below 2^31");
+        tiles += (p[i] + q[i] + 31) / 32;
+    }
+    if (tiles >= ((int64_t)1 << 31)) return bfail(nullptr, GCP_ERR_ARG, "too many samples in the batch");
+    gcp_batch *b = new (std::nothrow) gcp_batch();
+    if (!b) return bfail(nullptr, GCP_ERR_OOM, "host allocation");
+    b->n = nclients;
+    b->d = c0->d;
+    b->R = c0->R;
+    b->Rp = c0->Rp;
+    b->loss = c0->loss;
+    b->bf16 = c0->Abf != nullptr;
+    b->device = c0->device;
+    b->user_st = c0->st;
+    b->clients.assign(clients, clients + nclients);
+    b->p.assign(p, p + nclients);
+    b->q.assign(q, q + nclients);
+    b->total_tiles = (int)tiles;
+    b->cols = c0->cols;
+    std::vector<int4> specs((size_t)nclients * gcpb::kSpecWords);
+    std::vector<int> tstart(nclients + 1, 0);
+    std::vector<gcpb::ClientAux> aux(nclients);
+    for (int i = 0; i < nclients; ++i) {
+        gcp_ctx *c = clients[i];
+        double w_nz, w_z;
+        const gcpk::FusedSpec f = gcpk_make_spec(c, 0, p[i], q[i], true, nullptr, &w_nz, &w_z);
+        std::memcpy(&specs[(size_t)i * gcpb::kSpecWords], &f, sizeof(f));
+        const int nt = (int)((p[i] + q[i] + 31) / 32);
+        tstart[i + 1] = tstart[i] + nt;
+        gcpb::ClientAux &a = aux[i];
+        a.A = c->A;
+        a.B = c->B;
+        a.C = c->C;
+        a.G = c->G;
+        a.Grep = c->Grep;
+        a.Abf = c->Abf;
+        a.hot_row = c->hot_row;
+        a.Htot = c->Htot;
+        a.nparam = c->total_rows * c->Rp;
+        a.R = c->R;
+        a.Rp = c->Rp;
+        a.w_nz = w_nz;
+        a.w_z = w_z;
+        a.tile0 = tstart[i];
+        a.ntiles = nt;
+        b->max_param = std::max<int64_t>(b->max_param, a.nparam);
+        b->max_rep = std::max<int64_t>(b->max_rep, (int64_t)a.Htot * a.Rp);
+    }
+    cudaError_t e;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    if ((e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming)) ||
+        (e = cudaMalloc(&b->specs, specs.size() * sizeof(int4))) ||
+        (e = cudaMalloc(&b->tile_start, tstart.size() * sizeof(int))) ||
+        (e = cudaMalloc(&b->aux, aux.size() * sizeof(gcpb::ClientAux))) ||
+        (e = cudaMalloc(&b->tile_loss, (size_t)std::max(1, b->total_tiles) * sizeof(float2))) ||
+        (e = cudaMalloc(&b->client_loss, (size_t)nclients * sizeof(double))) ||
+        (e = cudaMalloc(&b->step, 2 * sizeof(uint64_t))) || (e = cudaMalloc(&b->adam, 5 * sizeof(double))) ||
+        (e = cudaMallocHost(&b->h_step, 2 * sizeof(uint64_t))) ||
+        (e = cudaMallocHost(&b->h_adam, 5 * sizeof(double))) ||
+        (e = cudaMallocHost(&b->h_loss, (size_t)nclients * sizeof(double))) ||
+        (e = cudaMemcpy(b->specs, specs.data(), specs.size() * sizeof(int4), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->tile_start, tstart.data(), tstart.size() * sizeof(int), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->aux, aux.data(), aux.size() * sizeof(gcpb::ClientAux), cudaMemcpyHostToDevice))) {
+        batch_free(b);
+        delete b;
+        if (prev >= 0) cudaSetDevice(prev);
+        return bfail(nullptr, e == cudaErrorMemoryAllocation ? GCP_ERR_OOM : GCP_ERR_CUDA,
+                     std::string("creating the batch: ") + cudaGetErrorString(e));
+    }
+    b->blocks = default_blocks(b, b->cols);
+    if (prev >= 0) cudaSetDevice(prev);
+    *out = b;
+    return GCP_OK;
+}
+
+void gcp_batch_destroy(gcp_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->st);
+    batch_free(b);
+    delete b;
+}
+
+const char *gcp_batch_last_error(const gcp_batch *b) { return b ? b->err.c_str() : g_batch_create_err.c_str(); }
+
+gcp_status gcp_batch_tune(gcp_batch *b, int32_t lane_cols, int32_t blocks) {
+    if (!b) return bfail(b, GCP_ERR_ARG, "NULL batch");
+    const int cols = lane_cols == 0 ? b->clients[0]->cols : lane_cols;
+    if (cols != 4 && !(cols == 8 && b->Rp >= 8)) return bfail(b, GCP_ERR_ARG, "lane_cols must be 0, 4 or 8 (8 needs rank > 4)");
+    if (blocks < 0) return bfail(b, GCP_ERR_ARG, "blocks must be >= 0");
+    b->cols = cols;
+    b->blocks = blocks == 0 ? default_blocks(b, cols) : blocks;
+    return GCP_OK;
+}
+
+gcp_status gcp_batch_local_steps(gcp_batch *b, int32_t tau, const gcp_adam_params *prm, uint64_t iter0, int64_t t0) {
+    if (!b || !prm) return bfail(b, GCP_ERR_ARG, "NULL argument");
+    if (tau < 1 || tau > 4096) return bfail(b, GCP_ERR_ARG, "tau must be in 1..4096");
+    if (t0 < 0) return bfail(b, GCP_ERR_ARG, "t0 must be >= 0");
+    if (!(prm->beta1 >= 0.0 && prm->beta1 < 1.0 && prm->beta2 >= 0.0 && prm->beta2 < 1.0 && prm->eps >= 0.0))
+        return bfail(b, GCP_ERR_ARG, "Adam parameters out of range");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    if (!b->graph || b->graph_tau != tau || b->graph_cols != b->cols || b->graph_blocks != b->blocks) {
+        if (b->graph) {
+            BCUDA(b, cudaStreamSynchronize(b->st));
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        BCUDA(b, cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+        gcp_status s = GCP_OK;
+        for (int k = 0; k < tau && !s; ++k) s = enqueue_step(b);
+        cudaError_t e = cudaStreamEndCapture(b->st, &g);
+        if (s) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        BCUDA(b, e);
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        BCUDA(b, e);
+        b->graph_tau = tau;
+        b->graph_cols = b->cols;
+        b->graph_blocks = b->blocks;
+    }
+    b->h_step[0] = iter0;
+    b->h_step[1] = (uint64_t)t0;
+    b->h_adam[0] = prm->lr;
+    b->h_adam[1] = prm->beta1;
+    b->h_adam[2] = prm->beta2;
+    b->h_adam[3] = prm->eps;
+    b->h_adam[4] = prm->lower;
+    BCUDA(b, cudaEventRecord(b->ev_in, b->user_st));  // after the clients' earlier work
+    BCUDA(b, cudaStreamWaitEvent(b->st, b->ev_in, 0));
+    BCUDA(b, cudaMemcpyAsync(b->step, b->h_step, 2 * sizeof(uint64_t), cudaMemcpyHostToDevice, b->st));
+    BCUDA(b, cudaMemcpyAsync(b->adam, b->h_adam, 5 * sizeof(double), cudaMemcpyHostToDevice, b->st));
+    BCUDA(b, cudaGraphLaunch(b->graph, b->st));
+    BCUDA(b, cudaEventRecord(b->ev_out, b->st));  // the clients' later work waits for the steps
+    BCUDA(b, cudaStreamWaitEvent(b->user_st, b->ev_out, 0));
+    if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+    return GCP_OK;
+}
+
+gcp_status gcp_batch_losses(gcp_batch *b, double *loss_out) {
+    if (!b || !loss_out) return bfail(b, GCP_ERR_ARG, "NULL argument");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    BCUDA(b, cudaMemcpyAsync(b->h_loss, b->client_loss, (size_t)b->n * sizeof(double), cudaMemcpyDeviceToHost,
+                             b->st));
+    BCUDA(b, cudaStreamSynchronize(b->st));
+    std::memcpy(loss_out, b->h_loss, (size_t)b->n * sizeof(double));
+    if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+    for (gcp_ctx *c : b->clients) {  // device errors of any client (sampler exhausted, ...)
+        gcp_status s = gcp_sync(c);
+        if (s) return bfail(b, s, std::string("client error: ") + gcp_last_error(c));
+    }
+    return GCP_OK;
+}
+
+}  // extern "C"

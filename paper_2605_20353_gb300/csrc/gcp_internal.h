@@ -154,3 +154,9 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f, int *blocks);
 // Record the message of a failed call that has no context; gcp_last_error(NULL)
 // returns it.
 void gcpk_set_noctx_error(const char *msg);
+
+// Fused-pass parameters of one sample set of a context (weights returned in
+// FP64), and the sample-count checks of the sampling calls.
+gcpk::FusedSpec gcpk_make_spec(const gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad,
+                               const float *dscale, double *w_nz_out, double *w_z_out);
+gcp_status gcpk_check_counts(gcp_ctx *c, int64_t p, int64_t q);

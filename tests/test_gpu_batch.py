@@ -1,0 +1,143 @@
+"""Batched independent clients (one multi-client launch per kernel, tau local
+steps in a CUDA graph) against the same clients stepped one at a time and
+against the FP64 oracle, client by client."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_err(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def bf16_round(a):
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16).astype(np.uint32).view(np.float32)
+
+
+@pytest.fixture(scope="module")
+def env(gpu_lib):
+    import torch
+
+    return gpu_lib, torch
+
+
+@pytest.fixture(scope="module")
+def shards():
+    cl = synth.client_batch(7, 5005, dim_lo=40, dim_hi=300, nnz_lo=300, nnz_hi=20000)
+    out = []
+    for i, (dims, coords, vals) in enumerate(cl):
+        f = synth.factors_uniform(dims, 16, 6000 + i, lo=0.1, hi=1.0)
+        S = max(1, math.ceil(len(vals) / 8))
+        out.append(dict(dims=dims, coords=coords, vals=vals, factors=f, p=S, q=S + 3 * i, seed=7000 + i))
+    return out
+
+
+def make(gcp, shards, dtype="fp32"):
+    ctxs = []
+    for s in shards:
+        c = gcp.gcp_create(s["dims"], s["coords"], s["vals"], 16, "poisson", dtype=dtype, seed=s["seed"])
+        c.set_factors(s["factors"])
+        ctxs.append(c)
+    return ctxs
+
+
+ADAM = dict(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, lower=0.0)
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "bf16"])
+def test_batch_matches_clients_stepped_one_at_a_time(env, shards, dtype):
+    gcp, torch = env
+    adam = gcp.AdamParams(**ADAM)
+    ref = make(gcp, shards, dtype)
+    for c, s in zip(ref, shards):
+        for k in range(3):
+            L, _ = c.grad(5 + k, s["p"], s["q"])
+            c.adam_step(adam, k + 1)
+        s["ref_loss"] = L
+    bat = make(gcp, shards, dtype)
+    b = gcp.GcpBatch(bat, [s["p"] for s in shards], [s["q"] for s in shards])
+    b.local_steps(3, adam, 5, 0)
+    losses = b.losses()
+    for c, r, s, L in zip(bat, ref, shards, losses):
+        A = np.concatenate([a.ravel() for a in c.get_factors()])
+        Ar = np.concatenate([a.ravel() for a in r.get_factors()])
+        assert rel_err(A, Ar) <= 1e-5
+        assert L == pytest.approx(s["ref_loss"], rel=1e-6)
+    b.close()
+
+
+def test_batch_one_step_matches_oracle_client_by_client(env, shards):
+    gcp, torch = env
+    adam = gcp.AdamParams(**ADAM)
+    bat = make(gcp, shards)
+    b = gcp.GcpBatch(bat, [s["p"] for s in shards], [s["q"] for s in shards])
+    b.local_steps(1, adam, 11, 0)
+    losses = b.losses()
+    for c, s, L in zip(bat, shards, losses):
+        idx, x, w, _ = oracle.stratified_samples(s["seed"], 11, s["p"], s["q"], s["dims"], s["coords"], s["vals"])
+        Lo, Go = oracle.sampled_loss_grad(s["dims"], s["factors"], "poisson", idx, x, w)
+        A = oracle.flat_factors(s["factors"])
+        B, C = np.zeros_like(A), np.zeros_like(A)
+        oracle.adam_step(A, B, C, np.concatenate([g.ravel() for g in Go]), **{
+            "lr": 1e-3, "beta1": 0.9, "beta2": 0.999, "eps": 1e-8, "lower": 0.0, "t": 1})
+        Ag = np.concatenate([a.ravel() for a in c.get_factors()])
+        assert L == pytest.approx(Lo, rel=1e-5)
+        assert rel_err(Ag, A) <= 1e-5
+    b.close()
+
+
+def test_graph_replays_continue_the_step_counters(env, shards):
+    gcp, torch = env
+    adam = gcp.AdamParams(**ADAM)
+    one = make(gcp, shards)
+    b1 = gcp.GcpBatch(one, [s["p"] for s in shards], [s["q"] for s in shards])
+    b1.local_steps(4, adam, 0, 0)
+    two = make(gcp, shards)
+    b2 = gcp.GcpBatch(two, [s["p"] for s in shards], [s["q"] for s in shards])
+    b2.local_steps(2, adam, 0, 0)
+    b2.local_steps(2, adam, 2, 2)  # graph reused, counters reset from the host
+    for c1, c2 in zip(one, two):
+        a1 = np.concatenate([a.ravel() for a in c1.get_factors()])
+        a2 = np.concatenate([a.ravel() for a in c2.get_factors()])
+        assert rel_err(a2, a1) <= 1e-5
+    b1.close()
+    b2.close()
+
+
+@pytest.mark.parametrize("cols,blocks", [(8, 0), (4, 3), (8, 1)])
+def test_tuning_knobs_do_not_change_results(env, shards, cols, blocks):
+    gcp, torch = env
+    adam = gcp.AdamParams(**ADAM)
+    base = make(gcp, shards)
+    b0 = gcp.GcpBatch(base, [s["p"] for s in shards], [s["q"] for s in shards])
+    b0.local_steps(2, adam, 3, 0)
+    tuned = make(gcp, shards)
+    b1 = gcp.GcpBatch(tuned, [s["p"] for s in shards], [s["q"] for s in shards])
+    b1.tune(cols, blocks)
+    b1.local_steps(2, adam, 3, 0)
+    for c0, c1 in zip(base, tuned):
+        a0 = np.concatenate([a.ravel() for a in c0.get_factors()])
+        a1 = np.concatenate([a.ravel() for a in c1.get_factors()])
+        assert rel_err(a1, a0) <= 1e-5
+    b0.close()
+    b1.close()
+
+
+def test_batch_rejects_mismatched_clients(env, shards):
+    gcp, torch = env
+    s0, s1 = shards[0], shards[1]
+    a = gcp.gcp_create(s0["dims"], s0["coords"], s0["vals"], 16, "poisson")
+    c = gcp.gcp_create(s1["dims"], s1["coords"], s1["vals"], 8, "poisson")
+    with pytest.raises(gcp.GcpError):
+        gcp.GcpBatch([a, c], [10, 10], [10, 10])
+    with pytest.raises(gcp.GcpError):
+        gcp.GcpBatch([a], [-1], [10])
