@@ -192,6 +192,114 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batched_variant(gcp, torch, stream, steps=20):
+    """64 independent 3-way client shards (federated clients simulated on one
+    GPU): mode sizes U{200..5000}, nnz log-uniform in [1e4, 2e6], values
+    1+Poisson(2), Poisson loss, rank 16, BF16 factors, p_c = q_c =
+    ceil(nnz_c / 8), tau = 8 local Adam steps per graph launch with autotuned
+    tiles, against the same clients stepped by 64 sequential plain launches."""
+    import synth
+    from paper_2605_20353_gb300 import autotune
+
+    shards = synth.cached("client_batch_64", lambda: synth.client_batch(64, 1005))
+    tau = 8
+    P = [math.ceil(len(v) / 8) for _, _, v in shards]
+    samples_per_step = 2 * sum(P)
+    adam = gcp.AdamParams(lr=1e-3, lower=0.0)
+
+    def make(dtype):
+        out = []
+        for i, (dims, coords, vals) in enumerate(shards):
+            c = gcp.gcp_create(dims, coords, vals, 16, "poisson", dtype=dtype, seed=5000 + i, stream=stream)
+            c.set_factors(synth.factors_uniform(dims, 16, 6000 + i, lo=0.1, hi=1.0))
+            out.append(c)
+        return out
+
+    res = {"workload": "64 clients, dims U{200..5000}^3, nnz log-uniform [1e4, 2e6], Poisson, rank 16",
+           "samples_per_local_step": samples_per_step, "tau": tau}
+    clients = make("bf16")
+    batch = gcp.GcpBatch(clients, P, P)
+    best, times = autotune.tune_batch(batch, adam, tau=tau, reps=2)
+    res["autotune"] = {"best_lane_cols": best[0], "best_blocks": best[1],
+                       "ms_per_step": {f"{c}x{g}": t for (c, g), t in times.items()}}
+    batch.local_steps(tau, adam, 0, 0)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        batch.local_steps(tau, adam, (k + 1) * tau, (k + 1) * tau)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    res["batched_graph"] = {"value": samples_per_step * tau * steps / (ms / 1e3), "unit": "samples/s"}
+    batch.close()
+    for c in clients:
+        c.close()
+    for dtype in ("bf16", "fp32"):
+        clients = make(dtype)
+        for i, c in enumerate(clients):
+            c.grad_async(0, P[i], P[i])
+            c.adam_step(adam, 1)
+        stream.synchronize()
+        nseq = max(2, steps // 4)
+        e0.record(stream)
+        for k in range(nseq * tau):
+            for i, c in enumerate(clients):
+                c.grad_async(k + 1, P[i], P[i])
+                c.adam_step(adam, k + 2)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[f"sequential_{dtype}"] = {"value": samples_per_step * tau * nseq / (ms / 1e3), "unit": "samples/s"}
+        for c in clients:
+            c.close()
+    res["speedup_vs_sequential_bf16"] = res["batched_graph"]["value"] / res["sequential_bf16"]["value"]
+    res["speedup_vs_sequential_fp32"] = res["batched_graph"]["value"] / res["sequential_fp32"]["value"]
+    return res
+
+
+def hbm_resident_variant(gcp, torch, stream, launches=20):
+    """Factors too large for L2: mode sizes near the paper's Amazon tensor
+    (4.8M x 1.7M x 1.1M; its third mode is shortened from 1.8M so the cell
+    count stays below 2^63), 2e7 uniform nonzeros with values 1+Poisson(2),
+    rank 16, Poisson loss, p = q = 2^20.  Gathers now come from HBM, so BF16
+    factor storage halves their bytes; fused-kernel time FP32 vs BF16."""
+    import numpy as np
+
+    import synth
+
+    dims = [4_800_000, 1_700_000, 1_100_000]
+
+    def gen():
+        coords, vals = synth.uniform_sparse(dims, 20_000_000, 1006, lam=2.0)
+        return dict(coords=coords, vals=vals)
+
+    w = synth.cached("hbm_resident_amazon_dims", gen)
+    fac = synth.factors_uniform(dims, 16, 2006, lo=0.1, hi=1.0)
+    S = 1 << 20
+    res = {"workload": "4.8Mx1.7Mx1.1M, 2e7 uniform nnz, rank 16, Poisson, p=q=2^20 (factors 486 MB FP32)"}
+    for dtype in ("fp32", "bf16"):
+        ctx = gcp.gcp_create(dims, w["coords"], w["vals"], 16, "poisson", dtype=dtype, seed=9, stream=stream)
+        ctx.set_factors(fac)
+        for i in range(3):
+            ctx.grad_async(i, S, S)
+        ctx.sync()
+        ctx.profile(True)
+        ctx.profile_read()
+        for i in range(launches):
+            ctx.grad_async(100 + i, S, S)
+        kms, nl = ctx.profile_read()
+        ctx.profile(False)
+        ctx.close()
+        per = kms / nl
+        bps = algorithmic_bytes_per_sample(3, 16, len(w["vals"]), float(np.prod(dims, dtype=np.float64)),
+                                           4 if dtype == "fp32" else 2)
+        res[dtype] = {"kernel_ms_per_launch": per, "samples_per_s": 2 * S / (per / 1e3),
+                      "achieved_gbs": bps * 2 * S / (per / 1e3) / 1e9, "bytes_per_sample": bps}
+    res["bf16_speedup"] = res["fp32"]["kernel_ms_per_launch"] / res["bf16"]["kernel_ms_per_launch"]
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -334,6 +442,9 @@ def run_ours(args):
             "variants": {"bf16_factors": {"value": bf16_value, "unit": "samples/s",
                                           "kernel_ms_per_launch": kms_bf / max(1, nl_bf),
                                           "achieved_gbs": bps_bf * S / (kms_bf / 1e3 / max(1, nl_bf)) / 1e9}}}
+    if not args.no_variants:
+        line["variants"]["batched_clients"] = batched_variant(gcp, torch, stream)
+        line["variants"]["hbm_resident_factors"] = hbm_resident_variant(gcp, torch, stream)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -348,6 +459,7 @@ def main():
     ap.add_argument("--nnz", type=float, default=None,
                     help="nonzero count of a smaller tensor of the same shape (profiling captures)")
     ap.add_argument("--kernel-only", action="store_true", help="time the step loop only (profiling)")
+    ap.add_argument("--no-variants", action="store_true", help="skip the batched and HBM-resident variants")
     ap.add_argument("--dtype", default="fp32", choices=["fp32", "bf16"], help="factor storage for --kernel-only")
     args = ap.parse_args()
     if args.warmup < 3:
