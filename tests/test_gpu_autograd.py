@@ -1,0 +1,77 @@
+"""The autograd function of the sampled GCP loss against the FP64 oracle:
+forward = sampled loss, backward = the fused MTTKRP adjoint (samples redrawn,
+Khatri-Rao rows recomputed), scaled by the incoming gradient."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def rel_err(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def env(gpu_lib):
+    import torch
+
+    from paper_2605_20353_gb300 import autograd
+
+    return gpu_lib, torch, autograd
+
+
+def check(env, ctx, factors_np, iteration, p, q, loss_name, oracle_samples, scale=1.0):
+    gcp, torch, ag = env
+    A = [torch.tensor(a, device="cuda", requires_grad=True) for a in factors_np]
+    loss = ag.sampled_loss(ctx, iteration, p, q, A)
+    (scale * loss).backward()
+    idx, x, w = oracle_samples
+    Lo, Go = oracle.sampled_loss_grad(ctx.dims, factors_np, loss_name, idx, x, w)
+    assert loss.dtype == torch.float64 and loss.dim() == 0
+    assert abs(loss.item() - Lo) <= TOL * abs(Lo)
+    for n, (a, g) in enumerate(zip(A, Go)):
+        assert rel_err(a.grad.cpu().numpy(), scale * g) <= TOL, n
+
+
+@pytest.mark.parametrize("scale", [1.0, -3.0])
+def test_autograd_dense_five_way(env, scale):
+    gcp, torch, ag = env
+    dims = [10, 9, 8, 4, 5]
+    X = synth.dense_cp_sinusoid(dims, 31, rank_true=4)
+    fac = synth.factors_normal(dims, 16, 32, std=0.6)
+    ctx = gcp.gcp_create_dense(dims, X, 16, "gaussian", seed=33)
+    check(env, ctx, fac, 4, 6000, 0, "gaussian", oracle.uniform_samples(33, 4, 6000, dims, X), scale=scale)
+    ctx.close()
+
+
+def test_autograd_sparse_poisson_and_second_call(env):
+    gcp, torch, ag = env
+    dims = [40, 30, 20]
+    coords, vals = synth.uniform_sparse(dims, 1500, 41, lam=2.0)
+    fac = synth.factors_uniform(dims, 8, 42, lo=0.1, hi=1.0)
+    ctx = gcp.gcp_create(dims, coords, vals, 8, "poisson", seed=43)
+    for it in (1, 2):  # the context is reused across graph evaluations
+        idx, x, w, _ = oracle.stratified_samples(43, it, 900, 1100, dims, coords, vals)
+        check(env, ctx, fac, it, 900, 1100, "poisson", (idx, x, w))
+    ctx.close()
+
+
+def test_autograd_dense_simulation_full_size(env):
+    """100x100x100x20x50 dense FP32 tensor (1e9 cells): rank-8 sinusoidal CP
+    signal + N(0, 0.1^2) noise, Gaussian loss, rank 16, 2^22 uniform samples;
+    loss and all five gradients against the oracle."""
+    gcp, torch, ag = env
+    dims = [100, 100, 100, 20, 50]
+    X = synth.dense_cp_sinusoid(dims, 1003, rank_true=8, sigma=0.1)
+    fac = synth.factors_normal(dims, 16, 2003, std=0.5)
+    ctx = gcp.gcp_create_dense(dims, X, 16, "gaussian", seed=3003)
+    s = 1 << 22
+    samples = oracle.uniform_samples(3003, 7, s, dims, X)
+    check(env, ctx, fac, 7, s, 0, "gaussian", samples)
+    ctx.close()

@@ -387,3 +387,26 @@ def test_oracle_matches_stored_golden():
     F, G = oracle.sampled_loss_grad(w["dims"], w["factors"], w["loss"], idx, x, wts)
     assert F == pytest.approx(g["sampled_loss"], rel=1e-12)
     assert [float(np.linalg.norm(a)) for a in G] == pytest.approx(g["sampled_grad_fro"], rel=1e-12)
+
+
+def test_dense_uniform_sampled_gradient_central_differences():
+    """The dense five-way case: uniform samples of a sinusoidal CP tensor,
+    Gaussian loss; the sampled gradient equals central differences (FP64,
+    h = 1e-6) of the sampled loss."""
+    dims = [6, 5, 4, 3, 4]
+    X = synth.dense_cp_sinusoid(dims, 12, rank_true=2)
+    factors = synth.factors_normal(dims, 3, 13, std=0.6)
+    idx, x, w = oracle.uniform_samples(14, 3, 400, dims, X)
+    _, G = oracle.sampled_loss_grad(dims, factors, "gaussian", idx, x, w)
+    h = 1e-6
+    rng = np.random.default_rng(15)
+    for _ in range(12):
+        n = int(rng.integers(0, 5))
+        i, r = int(idx[int(rng.integers(0, 400)), n]), int(rng.integers(0, 3))
+        fp = [a.astype(np.float64).copy() for a in factors]
+        fm = [a.astype(np.float64).copy() for a in factors]
+        fp[n][i, r] += h
+        fm[n][i, r] -= h
+        fd = (oracle.sampled_loss_grad(dims, fp, "gaussian", idx, x, w, grad=False)[0]
+              - oracle.sampled_loss_grad(dims, fm, "gaussian", idx, x, w, grad=False)[0]) / (2 * h)
+        assert G[n][i, r] == pytest.approx(fd, rel=1e-6, abs=1e-6 * max(1.0, abs(fd)))
