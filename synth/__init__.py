@@ -129,7 +129,7 @@ def bernoulli_logit_sparse(dims, nnz, seed, rank=16, logit_std=0.5, density=None
     M = math.prod(dims)
     rng = np.random.default_rng(seed)
     sig = (logit_std / math.sqrt(rank)) ** (1.0 / d)
-    U = [rng.normal(0.0, sig, size=(I, rank)).astype(np.float64) for I in dims]
+    U = [rng.normal(0.0, sig, size=(I, rank)).astype(np.float32) for I in dims]
     dens = nnz / M if density is None else density
     b = math.log(dens) - 0.5 * logit_std ** 2
     c = 4.0 * logit_std
@@ -140,10 +140,10 @@ def bernoulli_logit_sparse(dims, nnz, seed, rank=16, logit_std=0.5, density=None
         got = 0
         while got < n:
             cand = np.stack([rng.integers(0, I, size=chunk, dtype=np.int64) for I in dims], axis=1)
-            prod = np.ones((chunk, rank))
-            for k in range(d):
+            prod = U[0][cand[:, 0]]
+            for k in range(1, d):
                 prod *= U[k][cand[:, k]]
-            logit = prod.sum(axis=1) + b
+            logit = prod.sum(axis=1, dtype=np.float64) + b
             acc = rng.random(chunk) * top < 1.0 / (1.0 + np.exp(-logit))
             out.append(cand[acc])
             got += int(acc.sum())

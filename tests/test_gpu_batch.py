@@ -141,3 +141,33 @@ def test_batch_rejects_mismatched_clients(env, shards):
         gcp.GcpBatch([a, c], [10, 10], [10, 10])
     with pytest.raises(gcp.GcpError):
         gcp.GcpBatch([a], [-1], [10])
+
+
+def test_batch_of_64_clients_full_size_against_oracle(env):
+    """64 client shards, mode sizes U{200..5000}, nnz log-uniform in
+    [1e4, 2e6], 1+Poisson(2), Poisson loss, rank 16, BF16 factors with FP32
+    accumulation, p_c = q_c = ceil(nnz_c / 8): one local step of every client
+    in one graph launch, checked client by client against the oracle."""
+    gcp, torch = env
+    shards = synth.cached("client_batch_64", lambda: synth.client_batch(64, 1005))
+    adam = gcp.AdamParams(**ADAM)
+    clients, P, facs = [], [], []
+    for i, (dims, coords, vals) in enumerate(shards):
+        c = gcp.gcp_create(dims, coords, vals, 16, "poisson", dtype="bf16", seed=5000 + i)
+        f = synth.factors_uniform(dims, 16, 6000 + i, lo=0.1, hi=1.0)
+        c.set_factors(f)
+        clients.append(c)
+        facs.append(f)
+        P.append(math.ceil(len(vals) / 8))
+    b = gcp.GcpBatch(clients, P, P)
+    b.local_steps(1, adam, 9, 0)
+    losses = b.losses()
+    for i, ((dims, coords, vals), c) in enumerate(zip(shards, clients)):
+        idx, x, w, _ = oracle.stratified_samples(5000 + i, 9, P[i], P[i], dims, coords, vals)
+        Lo, Go = oracle.sampled_loss_grad(dims, [bf16_round(a) for a in facs[i]], "poisson", idx, x, w)
+        A = oracle.flat_factors(facs[i])
+        B, C = np.zeros_like(A), np.zeros_like(A)
+        oracle.adam_step(A, B, C, np.concatenate([g.ravel() for g in Go]), 1e-3, 0.9, 0.999, 1e-8, 0.0, 1)
+        assert losses[i] == pytest.approx(Lo, rel=1e-5), i
+        assert rel_err(np.concatenate([a.ravel() for a in c.get_factors()]), A) <= 1e-5, i
+    b.close()

@@ -365,3 +365,39 @@ def test_deterministic_mttkrp_parity_and_bit_stability(env, dims, R, loss, dtype
     assert rel_err(G1, Ga) <= TOL_FP32
     det.close()
     atom.close()
+
+
+@pytest.fixture(scope="module")
+def bernoulli_full():
+    def make():
+        dims = [10000, 10000, 1000]
+        coords, vals = synth.bernoulli_logit_sparse(dims, 20_000_000, 1004, rank=16)
+        return dict(dims=dims, coords=coords, vals=vals, factors=synth.factors_normal(dims, 64, 2004, std=0.5))
+    return synth.cached("bernoulli_full", make)
+
+
+@pytest.mark.parametrize("dtype,mttkrp", [("fp32", "atomic"), ("bf16", "atomic"), ("fp32", "deterministic")])
+def test_bernoulli_binary_full_size(env, bernoulli_full, dtype, mttkrp):
+    """10000x10000x1000 binary tensor with 2e7 ones from a rank-16 logistic
+    generator, Bernoulli-logit loss, rank 64, 2^21 ones + 2^21 zeros (hash
+    rejection); FP32 / BF16 factors, atomic / deterministic MTTKRP."""
+    gcp, torch = env
+    w = bernoulli_full
+    dims, p = w["dims"], 1 << 21
+    ctx = gcp.gcp_create(dims, w["coords"], w["vals"], 64, "bernoulli", dtype=dtype, mttkrp=mttkrp, seed=3004)
+    ctx.set_factors(w["factors"])
+    Lg, Gg = gpu_grad(gcp, torch, ctx, 2, p, p)
+    if mttkrp == "deterministic":
+        L2, G2 = gpu_grad(gcp, torch, ctx, 2, p, p)
+        assert L2 == Lg and np.array_equal(G2.view(np.uint32), Gg.view(np.uint32))
+    fac = [bf16_round(a) for a in w["factors"]] if dtype == "bf16" else w["factors"]
+    idx, x, wt, _ = oracle.stratified_samples(3004, 2, p, p, dims, w["coords"], w["vals"])
+    Lo, Go = oracle.sampled_loss_grad(dims, fac, "bernoulli", idx, x, wt)
+    assert abs(Lg - Lo) <= TOL_FP32 * abs(Lo)
+    for n, (a, b) in enumerate(zip(split(Gg, dims, 64), Go)):
+        assert rel_err(a, b) <= TOL_FP32, (n, rel_err(a, b))
+    if dtype == "bf16":
+        Lf, Gf = oracle.sampled_loss_grad(dims, w["factors"], "bernoulli", idx, x, wt)
+        assert abs(Lg - Lf) <= TOL_BF16 * abs(Lf)
+        assert rel_err(Gg, np.concatenate([g.ravel() for g in Gf])) <= TOL_BF16
+    ctx.close()
