@@ -300,6 +300,46 @@ def hbm_resident_variant(gcp, torch, stream, launches=20):
     return res
 
 
+def fused_vs_nonfused_variant(gcp, torch, stream, launches=10):
+    """The comparison of Sec. 5.1: fused vs non-fused sampling + MTTKRP with
+    semi-stratified samples, on a synthetic tensor with the arXiv tensor's
+    shape and nonzero count (172 x 25,000 x 300, 3e7 uniform nonzeros with
+    values 1+Poisson(2)), Poisson loss, rank 16, p = q varied."""
+    import synth
+
+    dims = [172, 25000, 300]
+
+    def gen():
+        coords, vals = synth.uniform_sparse(dims, 30_000_000, 1007, lam=2.0)
+        return dict(coords=coords, vals=vals)
+
+    w = synth.cached("arxiv_shape_3e7", gen)
+    fac = synth.factors_uniform(dims, 16, 2007, lo=0.1, hi=1.0)
+    res = {"workload": "172x25000x300, 3e7 uniform nnz, Poisson, rank 16, semi-stratified", "points": []}
+    ctxs = {m: gcp.gcp_create(dims, w["coords"], w["vals"], 16, "poisson", mttkrp=m, sampling="semi", seed=11,
+                              stream=stream) for m in ("atomic", "nonfused")}
+    for c in ctxs.values():
+        c.set_factors(fac)
+    for S in (1 << 16, 1 << 18, 1 << 20, 1 << 22):
+        pt = {"p": S, "q": S}
+        for m, c in ctxs.items():
+            for i in range(2):
+                c.grad_async(i, S, S)
+            c.sync()
+            c.profile(True)
+            c.profile_read()
+            for i in range(launches):
+                c.grad_async(10 + i, S, S)
+            kms, nl = c.profile_read()
+            c.profile(False)
+            pt["fused_ms" if m == "atomic" else "nonfused_ms"] = kms / nl
+        pt["fused_speedup"] = pt["nonfused_ms"] / pt["fused_ms"]
+        res["points"].append(pt)
+    for c in ctxs.values():
+        c.close()
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -445,6 +485,7 @@ def run_ours(args):
     if not args.no_variants:
         line["variants"]["batched_clients"] = batched_variant(gcp, torch, stream)
         line["variants"]["hbm_resident_factors"] = hbm_resident_variant(gcp, torch, stream)
+        line["variants"]["fused_vs_nonfused"] = fused_vs_nonfused_variant(gcp, torch, stream)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

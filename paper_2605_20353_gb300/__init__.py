@@ -24,7 +24,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_DUPLICATE"
           6: "ERR_SAMPLER_EXHAUSTED", 7: "ERR_NONFINITE", 8: "ERR_DOMAIN", 9: "ERR_STATE"}
 LOSSES = {"gaussian": 0, "poisson": 1, "bernoulli": 2, "gamma": 3}
 DTYPES = {"fp32": 0, "bf16": 1}
-MTTKRP = {"atomic": 0, "deterministic": 1}
+MTTKRP = {"atomic": 0, "deterministic": 1, "nonfused": 2}
 SAMPLING = {"stratified": 0, "semi": 1, "uniform": 2}
 GCP_ITER_OBJECTIVE = 2**64 - 1
 GCP_FIT_TRACE = 256

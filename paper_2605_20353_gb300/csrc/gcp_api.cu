@@ -97,6 +97,8 @@ void destroy_buffers(gcp_ctx *c) {
     cudaFree(c->dloss);
     cudaFree(c->status);
     cudaFree(c->det_scratch);
+    cudaFree(c->nf_coord);
+    cudaFree(c->nf_val);
     cudaFree(c->hot_slot);
     cudaFree(c->hot_row);
     cudaFree(c->Grep);
@@ -139,7 +141,8 @@ gcp_status init_common(gcp_ctx *c, int32_t ndim, const int64_t *dims, int32_t ra
     if (opt) c->opt = *opt;
     if (c->opt.factor_dtype != GCP_FP32 && c->opt.factor_dtype != GCP_BF16)
         return fail(nullptr, GCP_ERR_ARG, "unknown factor dtype");
-    if (c->opt.mttkrp != GCP_MTTKRP_ATOMIC && c->opt.mttkrp != GCP_MTTKRP_DETERMINISTIC)
+    if (c->opt.mttkrp != GCP_MTTKRP_ATOMIC && c->opt.mttkrp != GCP_MTTKRP_DETERMINISTIC &&
+        c->opt.mttkrp != GCP_MTTKRP_NONFUSED)
         return fail(nullptr, GCP_ERR_ARG, "unknown MTTKRP variant");
     if (c->opt.max_attempts < 0) return fail(nullptr, GCP_ERR_ARG, "max_attempts < 0");
     if (c->opt.max_attempts == 0) c->opt.max_attempts = 64;
@@ -292,11 +295,30 @@ gcp_status run_fused(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad,
     if (grad && c->opt.mttkrp == GCP_MTTKRP_DETERMINISTIC) {
         s = gcpk_det_grad(c, f, &blocks);
         if (s) return s;
+    } else if (grad && c->opt.mttkrp == GCP_MTTKRP_NONFUSED) {
+        const int64_t S = p + q;
+        if (S > c->nf_cap) {  // grow the gradient-tensor buffers
+            cudaFree(c->nf_coord);
+            cudaFree(c->nf_val);
+            c->nf_coord = nullptr;
+            c->nf_val = nullptr;
+            c->nf_cap = 0;
+            GCP_CUDA(c, cudaMalloc(&c->nf_coord, (size_t)S * c->d * 4));
+            GCP_CUDA(c, cudaMalloc(&c->nf_val, (size_t)S * 4));
+            c->nf_cap = S;
+        }
+        gcpk::FusedSpec m = f;  // pass 1: sampling, model, loss; writes the gradient tensor
+        m.G = nullptr;
+        m.Ycoord = c->nf_coord;
+        m.Yval = c->nf_val;
+        GCP_CUDA(c, gcpk::launch_fused(m, c->Abf != nullptr, c->cols, c->max_blocks, c->st, &blocks));
+        m.G = c->G;  // pass 2: MTTKRP of the stored gradient tensor
+        GCP_CUDA(c, gcpk::launch_mttkrp_nonfused(m, c->hot_slot, c->Abf != nullptr, c->cols, c->max_blocks, c->st));
     } else {
         GCP_CUDA(c, gcpk::launch_fused(f, c->Abf != nullptr, c->cols, c->max_blocks, c->st, &blocks));
     }
     if (stop) GCP_CUDA(c, cudaEventRecord(stop, c->st));
-    if (grad && c->opt.mttkrp == GCP_MTTKRP_ATOMIC)
+    if (grad && c->opt.mttkrp != GCP_MTTKRP_DETERMINISTIC)
         GCP_CUDA(c, gcpk::launch_fold_replicas(c->G, c->Grep, c->hot_row, c->Htot, c->Rp, c->st));
     GCP_CUDA(c, gcpk::launch_finish_loss(c->partials, blocks, w_nz, w_z, c->dloss, c->status, c->st));
     return GCP_OK;

@@ -71,6 +71,8 @@ cudaError_t launch_sample(const SampleSpec &s, int32_t *idx_out, float *x_out, f
 cudaError_t launch_fused(const FusedSpec &f, bool bf16, int cols, int max_blocks, cudaStream_t st,
                          int *blocks_used);
 cudaError_t launch_fold_replicas(float *G, float *Grep, const int *hot_row, int Htot, int Rp, cudaStream_t st);
+cudaError_t launch_mttkrp_nonfused(const FusedSpec &f, const int *hot_slot, bool bf16, int cols, int max_blocks,
+                                   cudaStream_t st);
 cudaError_t launch_finish_loss(const double *partials, int nblocks, double w_nz, double w_z, double *dloss,
                                int *status, cudaStream_t st);
 cudaError_t launch_adam(int64_t n, int Rp, int R, float *A, float *B, float *C, const float *G, float lr,
@@ -124,6 +126,11 @@ struct gcp_ctx {
     // deterministic MTTKRP scratch
     void *det_scratch = nullptr;
     size_t det_scratch_bytes = 0;
+
+    // non-fused MTTKRP: the materialised gradient tensor
+    int32_t *nf_coord = nullptr;
+    float *nf_val = nullptr;
+    int64_t nf_cap = 0;
 
     // gcp_fit: last accepted factors and moments
     float *bk_A = nullptr, *bk_B = nullptr, *bk_C = nullptr;

@@ -589,6 +589,96 @@ cudaError_t launch_fused(const FusedSpec &f, bool bf16, int cols, int max_blocks
     return cudaGetLastError();
 }
 
+// Non-fused MTTKRP (Sec. 3.1.2 before fusion): reads the gradient tensor the
+// sampling pass wrote (cells Ycoord, values Yval), gathers the factor rows
+// again and adds y prod_{k!=n} A_k(i_k,:) to every mode's rows, with the
+// same hot-row replicas as the fused pass (slots looked up by row).
+template <int D, typename TF, int COLS>
+__global__ void __launch_bounds__(kThreads) k_mttkrp_nonfused(const FusedSpec P, const int *__restrict__ hot_slot,
+                                                             int S) {
+    constexpr int NQ = COLS / 4;
+    const int lane = threadIdx.x & 31;
+    const int L = 1 << P.log2L;
+    const int glane = lane & (L - 1);
+    const int group = (blockIdx.x * blockDim.x + threadIdx.x) >> P.log2L;
+    const int ngroups = (gridDim.x * blockDim.x) >> P.log2L;
+    const int warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const TF *__restrict__ F = static_cast<const TF *>(P.F);
+    float *const grep = P.Grep ? P.Grep + (size_t)(warp0 & (kReplicas - 1)) * P.Htot * P.Rp : nullptr;
+    int col[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) col[q] = q * (P.Rp >> 1) + 4 * glane;
+    for (int s = group; s < S; s += ngroups) {
+        const float y = __ldg(P.Yval + s);
+        int ii[D], off[D];
+        float a[D][COLS];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            ii[k] = __ldg(P.Ycoord + (int64_t)s * D + k);
+            off[k] = (P.rowoff[k] + ii[k]) * P.Rp;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) Quad<TF>::load(F + off[k] + col[q], a[k] + 4 * q);
+        }
+        float suf[D][COLS];
+#pragma unroll
+        for (int v = 0; v < COLS; ++v) suf[D - 1][v] = 1.0f;
+#pragma unroll
+        for (int k = D - 2; k >= 0; --k)
+#pragma unroll
+            for (int v = 0; v < COLS; ++v) suf[k][v] = suf[k + 1][v] * a[k + 1][v];
+        float pre[COLS];
+#pragma unroll
+        for (int v = 0; v < COLS; ++v) pre[v] = y;
+#pragma unroll
+        for (int n = 0; n < D; ++n) {
+            const int hs = hot_slot ? __ldg(hot_slot + P.rowoff[n] + ii[n]) : -1;
+            float *g = hs >= 0 ? grep + hs * P.Rp : P.G + off[n];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                red_add_v4(g + col[q], pre[4 * q] * suf[n][4 * q], pre[4 * q + 1] * suf[n][4 * q + 1],
+                           pre[4 * q + 2] * suf[n][4 * q + 2], pre[4 * q + 3] * suf[n][4 * q + 3]);
+#pragma unroll
+            for (int v = 0; v < COLS; ++v) pre[v] *= a[n][v];
+        }
+    }
+}
+
+template <int D>
+static void launch_nonfused_d(const FusedSpec &f, const int *hot_slot, int S, bool bf16, int cols, int blocks,
+                              cudaStream_t st) {
+    if (bf16) {
+        if (cols == 8)
+            k_mttkrp_nonfused<D, __nv_bfloat16, 8><<<blocks, kThreads, 0, st>>>(f, hot_slot, S);
+        else
+            k_mttkrp_nonfused<D, __nv_bfloat16, 4><<<blocks, kThreads, 0, st>>>(f, hot_slot, S);
+    } else {
+        if (cols == 8)
+            k_mttkrp_nonfused<D, float, 8><<<blocks, kThreads, 0, st>>>(f, hot_slot, S);
+        else
+            k_mttkrp_nonfused<D, float, 4><<<blocks, kThreads, 0, st>>>(f, hot_slot, S);
+    }
+}
+
+cudaError_t launch_mttkrp_nonfused(const FusedSpec &f, const int *hot_slot, bool bf16, int cols, int max_blocks,
+                                   cudaStream_t st) {
+    const int S = (int)(f.s.p + f.s.q);
+    if (S == 0) return cudaSuccess;
+    const int64_t lanes = (int64_t)S << f.log2L;
+    int64_t want = (lanes + kThreads - 1) / kThreads;
+    const int blocks = (int)(want < max_blocks ? (want < 1 ? 1 : want) : max_blocks);
+    switch (f.s.d) {
+    case 2: launch_nonfused_d<2>(f, hot_slot, S, bf16, cols, blocks, st); break;
+    case 3: launch_nonfused_d<3>(f, hot_slot, S, bf16, cols, blocks, st); break;
+    case 4: launch_nonfused_d<4>(f, hot_slot, S, bf16, cols, blocks, st); break;
+    case 5: launch_nonfused_d<5>(f, hot_slot, S, bf16, cols, blocks, st); break;
+    case 6: launch_nonfused_d<6>(f, hot_slot, S, bf16, cols, blocks, st); break;
+    case 7: launch_nonfused_d<7>(f, hot_slot, S, bf16, cols, blocks, st); break;
+    case 8: launch_nonfused_d<8>(f, hot_slot, S, bf16, cols, blocks, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fold_replicas(float *G, float *Grep, const int *hot_row, int Htot, int Rp, cudaStream_t st) {
     if (Htot == 0) return cudaSuccess;
     k_fold_replicas<<<elementwise_blocks((int64_t)Htot * Rp), kThreads, 0, st>>>(G, Grep, hot_row, Htot, Rp);

@@ -401,3 +401,34 @@ def test_bernoulli_binary_full_size(env, bernoulli_full, dtype, mttkrp):
         assert abs(Lg - Lf) <= TOL_BF16 * abs(Lf)
         assert rel_err(Gg, np.concatenate([g.ravel() for g in Gf])) <= TOL_BF16
     ctx.close()
+
+
+# ------------------------------------------------------ non-fused MTTKRP
+@pytest.mark.parametrize("sampling,dtype", [("stratified", "fp32"), ("semi", "fp32"), ("stratified", "bf16")])
+def test_nonfused_mttkrp_matches_oracle_and_fused(env, sampling, dtype):
+    """Sampling writes the gradient tensor and a separate MTTKRP reads it;
+    the gradient equals the fused pass's (Sec. 3.1.2: fusion only removes
+    memory traffic)."""
+    gcp, torch = env
+    w = synth.workload_zipf_count(scale=0.01)
+    dims, p = w["dims"], 15000
+    res = {}
+    for mttkrp in ("nonfused", "atomic"):
+        ctx = gcp.gcp_create(dims, w["coords"], w["vals"], 32, "poisson", dtype=dtype, mttkrp=mttkrp,
+                             sampling=sampling, seed=31)
+        ctx.set_factors(w["factors"])
+        res[mttkrp] = gpu_grad(gcp, torch, ctx, 4, p, p + 7)
+        ctx.close()
+    fac = [bf16_round(a) for a in w["factors"]] if dtype == "bf16" else w["factors"]
+    if sampling == "semi":
+        idx, x, wt, semi = oracle.semi_stratified_samples(31, 4, p, p + 7, dims, w["coords"], w["vals"])
+    else:
+        idx, x, wt, _ = oracle.stratified_samples(31, 4, p, p + 7, dims, w["coords"], w["vals"])
+        semi = None
+    Lo, Go = oracle.sampled_loss_grad(dims, fac, "poisson", idx, x, wt, semi=semi)
+    L, G = res["nonfused"]
+    assert L == res["atomic"][0]  # same sampling pass, same fixed-order loss reduction
+    assert abs(L - Lo) <= TOL_FP32 * abs(Lo)
+    for n, (a, b) in enumerate(zip(split(G, dims, 32), Go)):
+        assert rel_err(a, b) <= TOL_FP32, n
+    assert rel_err(G, res["atomic"][1]) <= TOL_FP32
