@@ -53,7 +53,7 @@ struct FusedSpec {
 
 // Rows that many samples hit (Zipf heads, rows of small modes) are
 // accumulated in this many global replicas, then folded into G.
-constexpr int kReplicas = 32;
+constexpr int kReplicas = 64;
 
 struct LaunchCfg {
     int blocks;
