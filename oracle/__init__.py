@@ -84,6 +84,9 @@ def _load():
                                           _i32p, _f64p, _f64p, _u8p, _f64p]
     lib.orc_full_loss_grad.restype = ctypes.c_double
     lib.orc_full_loss_grad.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, _f64p, ctypes.c_int, _f64p, _f64p]
+    lib.orc_fedadam_server.restype = None
+    lib.orc_fedadam_server.argtypes = [ctypes.c_int64, ctypes.c_int64, _f64p, _f64p, _f64p, _f64p] + [
+        ctypes.c_double] * 5 + [ctypes.c_int64]
     lib.orc_adam_step.restype = None
     lib.orc_adam_step.argtypes = [ctypes.c_int64, _f64p, _f64p, _f64p, _f64p] + [ctypes.c_double] * 5 + [
         ctypes.c_int64]
@@ -268,6 +271,17 @@ def adam_step(A, B, C, G, lr, beta1, beta2, eps, lower, t):
     G = np.ascontiguousarray(G, dtype=np.float64)
     _load().orc_adam_step(A.size, _p(A, _f64p), _p(B, _f64p), _p(C, _f64p), _p(G, _f64p), lr, beta1, beta2, eps,
                           lower, t)
+
+
+def fedadam_server(M, U, B, C, lr, beta1, beta2, eps, lower, t):
+    """Algorithm 4 reconciliation in place on U, B, C (flat FP64); M is the
+    list of client models (flat FP64).  Returns the new U."""
+    Ms = np.ascontiguousarray(np.stack([np.asarray(m, np.float64) for m in M]))
+    for a in (U, B, C):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    _load().orc_fedadam_server(Ms.shape[0], Ms.shape[1], _p(Ms, _f64p), _p(U, _f64p), _p(B, _f64p), _p(C, _f64p),
+                               lr, beta1, beta2, eps, lower, t)
+    return U
 
 
 def densify(dims, coords, vals) -> np.ndarray:

@@ -396,3 +396,24 @@ void orc_adam_step(int64_t n, double *A, double *B, double *C, const double *G, 
             A[e] = lower;
     }
 }
+
+/* ------------------------------------------------------- GCP-FedAdam server */
+/* Reconciliation of Algorithm 4 for n clients of one model: the
+ * pseudo-gradient D = U - M_c, all-reduced as the mean over clients, updates
+ * the server model U with Adam (Algorithm 1, server moments B, C, step t);
+ * the caller then sets every client model to U.  M holds the n client models
+ * one after another (n x len). */
+void orc_fedadam_server(int64_t n, int64_t len, const double *M, double *U, double *B, double *C, double lr,
+                        double beta1, double beta2, double eps, double lower, int64_t t)
+{
+    double *D = (double *)malloc(sizeof(double) * (size_t)len);
+    for (int64_t e = 0; e < len; ++e) {
+        double mean = 0.0;
+        for (int64_t c = 0; c < n; ++c)
+            mean += M[c * len + e];
+        mean /= (double)n;
+        D[e] = U[e] - mean;
+    }
+    orc_adam_step(len, U, B, C, D, lr, beta1, beta2, eps, lower, t);
+    free(D);
+}

@@ -410,3 +410,37 @@ def test_dense_uniform_sampled_gradient_central_differences():
         fd = (oracle.sampled_loss_grad(dims, fp, "gaussian", idx, x, w, grad=False)[0]
               - oracle.sampled_loss_grad(dims, fm, "gaussian", idx, x, w, grad=False)[0]) / (2 * h)
         assert G[n][i, r] == pytest.approx(fd, rel=1e-6, abs=1e-6 * max(1.0, abs(fd)))
+
+
+# ------------------------------------------------------- FedAdam server
+def test_fedadam_server_fixed_point_and_sign_step():
+    """Algorithm 4's reconciliation: clients equal to U leave U and the server
+    moments at zero; with beta1 = beta2 = 0 and eps = 0 each step moves U by
+    lr * sign(U - mean(M)) (Adam's first step on D = U - mean of clients)."""
+    rng = np.random.default_rng(21)
+    U = rng.normal(size=50)
+    B, C = np.zeros(50), np.zeros(50)
+    oracle.fedadam_server([U.copy()] * 4, U, B, C, 0.1, 0.9, 0.999, 1e-8, -np.inf, 1)  # mean exact for 4
+    assert not np.any(B) and not np.any(C)
+    M = [U + rng.normal(size=50) for _ in range(4)]
+    mean = np.mean(M, axis=0)
+    U0 = U.copy()
+    oracle.fedadam_server(M, U, np.zeros(50), np.zeros(50), 0.1, 0.0, 0.0, 0.0, -np.inf, 1)
+    np.testing.assert_allclose(U, U0 - 0.1 * np.sign(U0 - mean), rtol=0, atol=1e-15)
+
+
+def test_fedadam_server_is_adam_on_mean_pseudo_gradient():
+    """Against torch.optim.Adam (eps = 0) fed the mean pseudo-gradient."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(22)
+    U = rng.normal(size=40)
+    B, C = np.zeros(40), np.zeros(40)
+    p = torch.nn.Parameter(torch.tensor(U.copy()))
+    opt = torch.optim.Adam([p], lr=0.05, betas=(0.7, 0.9), eps=0.0)
+    for t in range(1, 5):
+        M = [U + rng.normal(size=40) for _ in range(3)]
+        D = U - np.mean(M, axis=0)
+        oracle.fedadam_server(M, U, B, C, 0.05, 0.7, 0.9, 0.0, -np.inf, t)
+        p.grad = torch.tensor(D)
+        opt.step()
+        np.testing.assert_allclose(U, p.detach().numpy(), rtol=1e-12, atol=1e-14)
