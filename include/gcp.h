@@ -279,6 +279,21 @@ gcp_status gcp_batch_local_steps(gcp_batch *batch, int32_t tau, const gcp_adam_p
  * Synchronises; returns any pending device error of a client. */
 gcp_status gcp_batch_losses(gcp_batch *batch, double *loss_out);
 
+/* GCP-FedAdam reconciliation (Alg. 4) for a batch whose clients are shards
+ * of one model (identical mode sizes).  The batch keeps the server model U
+ * and its Adam moments.
+ * gcp_batch_server_init: U = client 0's factors, server moments cleared,
+ *   every client's factors set to U.
+ * gcp_batch_server_step: the pseudo-gradient D = U - M_c, all-reduced as the
+ *   mean over clients (summed in client order), updates U with Adam
+ *   (Algorithm 1, hyperparameters prm -- its lr is the meta-rate -- and
+ *   server step t >= 1); then every client's factors are set to U (M <- U).
+ *   The clients' own Adam moments are kept.
+ * Both are asynchronous on the clients' stream; GCP_ERR_STATE before init,
+ * GCP_ERR_ARG for clients of different shapes. */
+gcp_status gcp_batch_server_init(gcp_batch *batch);
+gcp_status gcp_batch_server_step(gcp_batch *batch, const gcp_adam_params *prm, int64_t t);
+
 /* Sampled loss and gradient of a caller-supplied sample list, allocating
  * nothing.  The paper has no counterpart: it exists for callers that cannot
  * allocate device memory -- code that runs under a device-memory budget

@@ -97,6 +97,8 @@ SIGNATURES = {
     "gcp_batch_tune": (_i32, [_vp, _i32, _i32]),
     "gcp_batch_local_steps": (_i32, [_vp, _i32, ctypes.POINTER(gcp_adam_params), _u64, _i64]),
     "gcp_batch_losses": (_i32, [_vp, _vp]),
+    "gcp_batch_server_init": (_i32, [_vp]),
+    "gcp_batch_server_step": (_i32, [_vp, ctypes.POINTER(gcp_adam_params), _i64]),
     "gcp_grad_samples_noalloc": (_i32, [_i32, _vp, _i32, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
@@ -357,6 +359,15 @@ class GcpBatch:
     def local_steps(self, tau, adam: AdamParams, iter0, t0):
         c = adam.c()
         self._check(load().gcp_batch_local_steps(self.handle, tau, ctypes.byref(c), iter0, t0))
+
+    def server_init(self):
+        """GCP-FedAdam: server model = client 0's factors, broadcast to all."""
+        self._check(load().gcp_batch_server_init(self.handle))
+
+    def server_step(self, adam: AdamParams, t: int):
+        """GCP-FedAdam reconciliation (Alg. 4) with the server Adam step t."""
+        c = adam.c()
+        self._check(load().gcp_batch_server_step(self.handle, ctypes.byref(c), t))
 
     def losses(self):
         out = np.zeros(len(self.clients), dtype=np.float64)

@@ -360,6 +360,50 @@ __global__ void k_batch_advance(uint64_t *step) {
     step[1] += 1;
 }
 
+// ------------------------------------------------------ GCP-FedAdam server
+// Clients of one model (identical shapes): U is the server model with Adam
+// moments Bs, Cs.  Init: U = client 0's factors, moments cleared, every
+// client set to U.
+__global__ void k_fed_init(const ClientAux *__restrict__ aux, int n, float *U, float *Bs, float *Cs) {
+    const ClientAux &a0 = aux[0];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a0.nparam; e += (int64_t)gridDim.x * blockDim.x) {
+        const float u = a0.A[e];
+        U[e] = u;
+        Bs[e] = 0.0f;
+        Cs[e] = 0.0f;
+        for (int c = 1; c < n; ++c) {
+            aux[c].A[e] = u;
+            if (aux[c].Abf) static_cast<__nv_bfloat16 *>(aux[c].Abf)[e] = __float2bfloat16_rn(u);
+        }
+    }
+}
+
+// Reconciliation of Algorithm 4: D = U - mean_c M_c (clients summed in
+// order), Adam (Algorithm 1) on U with the server hyperparameters
+// c = {lr, beta1, beta2, 1/(1-beta1^t), 1/(1-beta2^t), eps, lower}, then
+// M_c = U for every client.  Padded columns stay zero.
+__global__ void k_fed_server(const ClientAux *__restrict__ aux, int n, float *U, float *Bs, float *Cs,
+                             const float *__restrict__ c7) {
+    const ClientAux &a0 = aux[0];
+    const float lr = c7[0], b1 = c7[1], b2 = c7[2], c1 = c7[3], c2 = c7[4], eps = c7[5], lower = c7[6];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a0.nparam; e += (int64_t)gridDim.x * blockDim.x) {
+        if ((int)(e % a0.Rp) >= a0.R) continue;
+        float sum = 0.0f;
+        for (int c = 0; c < n; ++c) sum += aux[c].A[e];
+        const float d = U[e] - sum / (float)n;
+        const float b = b1 * Bs[e] + (1.0f - b1) * d;
+        const float cc = b2 * Cs[e] + (1.0f - b2) * d * d;
+        Bs[e] = b;
+        Cs[e] = cc;
+        const float u = fmaxf(U[e] - lr * ((b * c1) / sqrtf(cc * c2 + eps)), lower);
+        U[e] = u;
+        for (int c = 0; c < n; ++c) {
+            aux[c].A[e] = u;
+            if (aux[c].Abf) static_cast<__nv_bfloat16 *>(aux[c].Abf)[e] = __float2bfloat16_rn(u);
+        }
+    }
+}
+
 template <int D>
 cudaError_t launch_fused_d(bool bf16, int cols, int blocks, const int4 *specs, const int *tile_start, int n,
                            int total_tiles, int log2L, int Rp, const uint64_t *step, float2 *tile_loss,
@@ -419,6 +463,8 @@ struct gcp_batch {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_tau = 0, graph_cols = 0, graph_blocks = 0;
+    float *U = nullptr, *Bs = nullptr, *Cs = nullptr;  // FedAdam server model and moments
+    float *fed_c = nullptr, *h_fed_c = nullptr;        // server Adam constants (device, pinned)
     std::string err;
 };
 
@@ -454,6 +500,11 @@ void batch_free(gcp_batch *b) {
     cudaFreeHost(b->h_step);
     cudaFreeHost(b->h_adam);
     cudaFreeHost(b->h_loss);
+    cudaFree(b->U);
+    cudaFree(b->Bs);
+    cudaFree(b->Cs);
+    cudaFree(b->fed_c);
+    cudaFreeHost(b->h_fed_c);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->st) cudaStreamDestroy(b->st);
@@ -700,6 +751,64 @@ gcp_status gcp_batch_losses(gcp_batch *b, double *loss_out) {
         gcp_status s = gcp_sync(c);
         if (s) return bfail(b, s, std::string("client error: ") + gcp_last_error(c));
     }
+    return GCP_OK;
+}
+
+gcp_status gcp_batch_server_init(gcp_batch *b) {
+    if (!b) return bfail(b, GCP_ERR_ARG, "NULL batch");
+    const gcp_ctx *c0 = b->clients[0];
+    for (const gcp_ctx *c : b->clients)
+        for (int k = 0; k < b->d; ++k)
+            if (c->dims[k] != c0->dims[k])
+                return bfail(b, GCP_ERR_ARG, "the FedAdam server needs clients of one model shape");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    const size_t bytes = (size_t)b->max_param * sizeof(float);
+    if (!b->U) {
+        BCUDA(b, cudaMalloc(&b->U, bytes));
+        BCUDA(b, cudaMalloc(&b->Bs, bytes));
+        BCUDA(b, cudaMalloc(&b->Cs, bytes));
+        BCUDA(b, cudaMalloc(&b->fed_c, 8 * sizeof(float)));
+        BCUDA(b, cudaMallocHost(&b->h_fed_c, 8 * sizeof(float)));
+    }
+    BCUDA(b, cudaEventRecord(b->ev_in, b->user_st));
+    BCUDA(b, cudaStreamWaitEvent(b->st, b->ev_in, 0));
+    const int blocks = (int)std::min<int64_t>(1024, (b->max_param + gcpb::kThreads - 1) / gcpb::kThreads);
+    gcpb::k_fed_init<<<blocks, gcpb::kThreads, 0, b->st>>>(b->aux, b->n, b->U, b->Bs, b->Cs);
+    BCUDA(b, cudaGetLastError());
+    BCUDA(b, cudaEventRecord(b->ev_out, b->st));
+    BCUDA(b, cudaStreamWaitEvent(b->user_st, b->ev_out, 0));
+    if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+    return GCP_OK;
+}
+
+gcp_status gcp_batch_server_step(gcp_batch *b, const gcp_adam_params *prm, int64_t t) {
+    if (!b || !prm) return bfail(b, GCP_ERR_ARG, "NULL argument");
+    if (!b->U) return bfail(b, GCP_ERR_STATE, "call gcp_batch_server_init first");
+    if (t < 1) return bfail(b, GCP_ERR_ARG, "server step t must be >= 1");
+    if (!(prm->beta1 >= 0.0 && prm->beta1 < 1.0 && prm->beta2 >= 0.0 && prm->beta2 < 1.0 && prm->eps >= 0.0))
+        return bfail(b, GCP_ERR_ARG, "Adam parameters out of range");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    BCUDA(b, cudaStreamSynchronize(b->st));  // the pinned constants are reused
+    b->h_fed_c[0] = (float)prm->lr;
+    b->h_fed_c[1] = (float)prm->beta1;
+    b->h_fed_c[2] = (float)prm->beta2;
+    b->h_fed_c[3] = (float)(1.0 / (1.0 - std::pow(prm->beta1, (double)t)));
+    b->h_fed_c[4] = (float)(1.0 / (1.0 - std::pow(prm->beta2, (double)t)));
+    b->h_fed_c[5] = (float)prm->eps;
+    b->h_fed_c[6] = (float)prm->lower;
+    BCUDA(b, cudaEventRecord(b->ev_in, b->user_st));
+    BCUDA(b, cudaStreamWaitEvent(b->st, b->ev_in, 0));
+    BCUDA(b, cudaMemcpyAsync(b->fed_c, b->h_fed_c, 8 * sizeof(float), cudaMemcpyHostToDevice, b->st));
+    const int blocks = (int)std::min<int64_t>(1024, (b->max_param + gcpb::kThreads - 1) / gcpb::kThreads);
+    gcpb::k_fed_server<<<blocks, gcpb::kThreads, 0, b->st>>>(b->aux, b->n, b->U, b->Bs, b->Cs, b->fed_c);
+    BCUDA(b, cudaGetLastError());
+    BCUDA(b, cudaEventRecord(b->ev_out, b->st));
+    BCUDA(b, cudaStreamWaitEvent(b->user_st, b->ev_out, 0));
+    if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
     return GCP_OK;
 }
 

@@ -171,3 +171,60 @@ def test_batch_of_64_clients_full_size_against_oracle(env):
         assert losses[i] == pytest.approx(Lo, rel=1e-5), i
         assert rel_err(np.concatenate([a.ravel() for a in c.get_factors()]), A) <= 1e-5, i
     b.close()
+
+
+def test_fedadam_rounds_match_oracle(env):
+    """GCP-FedAdam (Alg. 4) on four shards of one tensor: server init, tau = 2
+    local steps, reconciliation, again; every client's model and the server
+    model against the FP64 oracle replaying the same rounds."""
+    gcp, torch = env
+    dims, R = [80, 60, 40], 8
+    coords, vals = synth.uniform_sparse(dims, 6000, 77, lam=2.0)
+    parts = [(coords[i::4], vals[i::4]) for i in range(4)]
+    F0 = synth.factors_uniform(dims, R, 78, lo=0.1, hi=1.0)
+    local = gcp.AdamParams(lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, lower=0.0)
+    server = gcp.AdamParams(lr=3e-2, beta1=0.6, beta2=0.99, eps=1e-8, lower=0.0)
+    clients = []
+    for i, (c, v) in enumerate(parts):
+        ctx = gcp.gcp_create(dims, c, v, R, "poisson", seed=90 + i)
+        ctx.set_factors(F0 if i == 0 else synth.factors_uniform(dims, R, 200 + i))
+        clients.append(ctx)
+    P = [len(v) // 2 for _, v in parts]
+    b = gcp.GcpBatch(clients, P, P)
+    b.server_init()
+    # oracle state
+    U = oracle.flat_factors(F0)
+    Bs, Cs = np.zeros_like(U), np.zeros_like(U)
+    Mb = [np.zeros_like(U) for _ in parts]
+    Mc = [np.zeros_like(U) for _ in parts]
+    A = [U.copy() for _ in parts]
+    it, t_local = 0, 0
+    for rnd in (1, 2):
+        b.local_steps(2, local, it, t_local)
+        b.server_step(server, rnd)
+        for i, (c, v) in enumerate(parts):
+            for k in range(2):
+                idx, x, w, _ = oracle.stratified_samples(90 + i, it + k, P[i], P[i], dims, c, v)
+                _, G = oracle.sampled_loss_grad(dims, oracle.split_factors(A[i], dims, R), "poisson", idx, x, w)
+                oracle.adam_step(A[i], Mb[i], Mc[i], np.concatenate([g.ravel() for g in G]), 1e-2, 0.9, 0.999,
+                                 1e-8, 0.0, t_local + k + 1)
+        oracle.fedadam_server(A, U, Bs, Cs, 3e-2, 0.6, 0.99, 1e-8, 0.0, rnd)
+        A = [U.copy() for _ in parts]
+        it += 2
+        t_local += 2
+        tol = 1e-5 if rnd == 1 else 1e-4
+        for ctx in clients:
+            Ag = np.concatenate([a.ravel() for a in ctx.get_factors()])
+            assert rel_err(Ag, U) <= tol, (rnd, rel_err(Ag, U))
+    b.close()
+
+
+def test_fedadam_requires_one_model_shape(env, shards):
+    gcp, torch = env
+    cl = make(gcp, shards[:2])
+    b = gcp.GcpBatch(cl, [10, 10], [10, 10])
+    with pytest.raises(gcp.GcpError):
+        b.server_init()
+    with pytest.raises(gcp.GcpError):
+        b.server_step(gcp.AdamParams(), 1)
+    b.close()
