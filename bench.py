@@ -381,8 +381,7 @@ def run_ours(args):
 
     def timed_loop(ctx, steps, warmup, profile):
         for i in range(warmup):
-            ctx.grad_async(10_000 + i, p, q)
-            ctx.adam_step(adam, i + 1)
+            ctx.step(10_000 + i, p, q, adam, i + 1)
         ctx.sync()
         if profile:
             ctx.profile(True)
@@ -393,8 +392,7 @@ def run_ours(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for i in range(steps):
-            ctx.grad_async(i, p, q)
-            ctx.adam_step(adam, warmup + i + 1)
+            ctx.step(i, p, q, adam, warmup + i + 1)
         e1.record(stream)
         torch.cuda.synchronize()
         if dist:
@@ -473,12 +471,12 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "samples_per_step": S, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (1.6 GB records, 2.1 GB hash set); factors and gradient "
                              "(0.6 MB each) stay L2-resident across steps as in training",
-                       "step": "fused sampled gradient + Adam"},
+                       "step": "gcp_step: fused sampled gradient + one epilogue (loss, replica fold, Adam)"},
             "roofline": roofline, "cpu_baseline": base,
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(A_host.numel() * 4),
                     "d2h_bytes_per_step": int(G_host.numel() * 4 + 8)},
-            # per step: k_fused, k_fold_replicas, k_finish_loss, k_adam (plus one G memset)
-            "gpu_launches": 4 * args.steps, "clocks": clocks,
+            # per step (gcp_step): k_fused and the k_post_step epilogue
+            "gpu_launches": 2 * args.steps, "clocks": clocks,
             "variants": {"bf16_factors": {"value": bf16_value, "unit": "samples/s",
                                           "kernel_ms_per_launch": kms_bf / max(1, nl_bf),
                                           "achieved_gbs": bps_bf * S / (kms_bf / 1e3 / max(1, nl_bf)) / 1e9}}}

@@ -224,6 +224,16 @@ gcp_status gcp_grad_async(gcp_ctx *ctx, uint64_t iter, int64_t p, int64_t q, con
  * Sec. 3.1.3) with the gradient held by the context, t >= 1. */
 gcp_status gcp_adam_step(gcp_ctx *ctx, const gcp_adam_params *prm, int64_t t);
 
+/* One training step (Algorithm 2's iteration on one GPU): the sampled
+ * gradient of iteration `iter` (as gcp_grad) followed by Adam step t (as
+ * gcp_adam_step).  With the atomic MTTKRP the step is two launches: the
+ * fused pass, then one epilogue that finishes the loss, folds the hot-row
+ * replicas, applies Adam and clears the gradient for the next step -- so
+ * after gcp_step the context's gradient buffer is zero, not the step's G.
+ * dloss_out (device, nullable) receives the sampled loss.  Asynchronous. */
+gcp_status gcp_step(gcp_ctx *ctx, uint64_t iter, int64_t p, int64_t q, const gcp_adam_params *prm, int64_t t,
+                    double *dloss_out);
+
 /* Wait for the context's stream and return (and clear) any device error. */
 gcp_status gcp_sync(gcp_ctx *ctx);
 

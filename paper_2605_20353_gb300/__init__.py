@@ -87,6 +87,7 @@ SIGNATURES = {
     "gcp_grad": (_i32, [_vp, _u64, _i64, _i64, _vp, _vp]),
     "gcp_grad_async": (_i32, [_vp, _u64, _i64, _i64, _vp, _vp, _vp]),
     "gcp_adam_step": (_i32, [_vp, ctypes.POINTER(gcp_adam_params), _i64]),
+    "gcp_step": (_i32, [_vp, _u64, _i64, _i64, ctypes.POINTER(gcp_adam_params), _i64, _vp]),
     "gcp_sync": (_i32, [_vp]),
     "gcp_fit": (_i32, [_vp, ctypes.POINTER(gcp_fit_params), ctypes.POINTER(gcp_fit_report)]),
     "gcp_profile": (_i32, [_vp, _i32]),
@@ -266,6 +267,11 @@ class GcpContext:
     def adam_step(self, prm: AdamParams, t: int):
         c = prm.c()
         _check(load().gcp_adam_step(self.handle, ctypes.byref(c), t), self.handle)
+
+    def step(self, iter, p, q, prm: AdamParams, t: int, dloss=None):
+        """Sampled gradient + Adam step t in one call (G is cleared after)."""
+        c = prm.c()
+        _check(load().gcp_step(self.handle, iter, p, q, ctypes.byref(c), t, _ptr(dloss)), self.handle)
 
     def sync(self):
         _check(load().gcp_sync(self.handle), self.handle)

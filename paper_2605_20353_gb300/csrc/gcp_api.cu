@@ -288,7 +288,10 @@ gcp_status run_fused(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad,
     if (s) return s;
     double w_nz, w_z;
     gcpk::FusedSpec f = gcpk_make_spec(c, iter, p, q, grad, dscale, &w_nz, &w_z);
-    if (grad) GCP_CUDA(c, cudaMemsetAsync(c->G, 0, (size_t)c->total_rows * c->Rp * 4, c->st));
+    if (grad) {
+        GCP_CUDA(c, cudaMemsetAsync(c->G, 0, (size_t)c->total_rows * c->Rp * 4, c->st));
+        c->g_clear = false;
+    }
     int blocks = 0;
     cudaEvent_t stop = nullptr;
     if ((s = prof_begin(c, &stop))) return s;
@@ -321,6 +324,68 @@ gcp_status run_fused(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad,
     if (grad && c->opt.mttkrp != GCP_MTTKRP_DETERMINISTIC)
         GCP_CUDA(c, gcpk::launch_fold_replicas(c->G, c->Grep, c->hot_row, c->Htot, c->Rp, c->st));
     GCP_CUDA(c, gcpk::launch_finish_loss(c->partials, blocks, w_nz, w_z, c->dloss, c->status, c->st));
+    return GCP_OK;
+}
+
+gcp_status adam_step_impl(gcp_ctx *c, const gcp_adam_params *prm, int64_t t) {
+    if (t < 1) return fail(c, GCP_ERR_ARG, "Adam step t must be >= 1");
+    if (!(prm->beta1 >= 0.0 && prm->beta1 < 1.0 && prm->beta2 >= 0.0 && prm->beta2 < 1.0 && prm->eps >= 0.0))
+        return fail(c, GCP_ERR_ARG, "Adam parameters out of range");
+    DeviceGuard g(c->device);
+    const double c1 = 1.0 - std::pow(prm->beta1, (double)t), c2 = 1.0 - std::pow(prm->beta2, (double)t);
+    GCP_CUDA(c, gcpk::launch_adam((int64_t)c->total_rows * c->Rp, c->Rp, c->R, c->A, c->B, c->C, c->G,
+                                  (float)prm->lr, (float)prm->beta1, (float)prm->beta2, (float)(1.0 / c1),
+                                  (float)(1.0 / c2), (float)prm->eps, (float)prm->lower, c->Abf, c->st));
+    return GCP_OK;
+}
+
+
+// One training step: sampled gradient of iteration `iter` and Adam step t.
+// With the atomic MTTKRP the epilogue (replica fold, loss finish, Adam, G
+// cleared for the next step) is one launch after the fused pass.
+gcp_status do_step(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, const gcp_adam_params *prm, int64_t t) {
+    gcp_status s;
+    if (c->opt.mttkrp != GCP_MTTKRP_ATOMIC) {
+        if ((s = run_fused(c, iter, p, q, true, nullptr))) return s;
+        return adam_step_impl(c, prm, t);
+    }
+    if ((s = check_counts(c, p, q))) return s;
+    double w_nz, w_z;
+    const gcpk::FusedSpec f = gcpk_make_spec(c, iter, p, q, true, nullptr, &w_nz, &w_z);
+    if (!c->g_clear) GCP_CUDA(c, cudaMemsetAsync(c->G, 0, (size_t)c->total_rows * c->Rp * 4, c->st));
+    int blocks = 0;
+    cudaEvent_t stop = nullptr;
+    if ((s = prof_begin(c, &stop))) return s;
+    GCP_CUDA(c, gcpk::launch_fused(f, c->Abf != nullptr, c->cols, c->max_blocks, c->st, &blocks));
+    if (stop) GCP_CUDA(c, cudaEventRecord(stop, c->st));
+    const double c1 = 1.0 - std::pow(prm->beta1, (double)t), c2 = 1.0 - std::pow(prm->beta2, (double)t);
+    gcpk::PostSpec ps{};
+    ps.n = (int64_t)c->total_rows * c->Rp;
+    ps.Rp = c->Rp;
+    ps.R = c->R;
+    ps.Htot = c->Htot;
+    ps.G = c->G;
+    ps.Grep = c->Grep;
+    ps.A = c->A;
+    ps.B = c->B;
+    ps.C = c->C;
+    ps.Abf = c->Abf;
+    ps.hot_slot = c->hot_slot;
+    ps.lr = (float)prm->lr;
+    ps.beta1 = (float)prm->beta1;
+    ps.beta2 = (float)prm->beta2;
+    ps.c1inv = (float)(1.0 / c1);
+    ps.c2inv = (float)(1.0 / c2);
+    ps.eps = (float)prm->eps;
+    ps.lower = (float)prm->lower;
+    ps.partials = c->partials;
+    ps.nblocks = blocks;
+    ps.w_nz = w_nz;
+    ps.w_z = w_z;
+    ps.dloss = c->dloss;
+    ps.status = c->status;
+    GCP_CUDA(c, gcpk::launch_post_step(ps, c->st));
+    c->g_clear = true;
     return GCP_OK;
 }
 
@@ -633,14 +698,21 @@ gcp_status gcp_grad_async(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, const
 
 gcp_status gcp_adam_step(gcp_ctx *c, const gcp_adam_params *prm, int64_t t) {
     if (!c || !prm) return fail(c, GCP_ERR_ARG, "NULL argument");
+    DeviceGuard g(c->device);
+    return adam_step_impl(c, prm, t);
+}
+
+gcp_status gcp_step(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, const gcp_adam_params *prm, int64_t t,
+                    double *dloss_out) {
+    if (!c || !prm) return fail(c, GCP_ERR_ARG, "NULL argument");
     if (t < 1) return fail(c, GCP_ERR_ARG, "Adam step t must be >= 1");
     if (!(prm->beta1 >= 0.0 && prm->beta1 < 1.0 && prm->beta2 >= 0.0 && prm->beta2 < 1.0 && prm->eps >= 0.0))
         return fail(c, GCP_ERR_ARG, "Adam parameters out of range");
     DeviceGuard g(c->device);
-    const double c1 = 1.0 - std::pow(prm->beta1, (double)t), c2 = 1.0 - std::pow(prm->beta2, (double)t);
-    GCP_CUDA(c, gcpk::launch_adam((int64_t)c->total_rows * c->Rp, c->Rp, c->R, c->A, c->B, c->C, c->G,
-                                  (float)prm->lr, (float)prm->beta1, (float)prm->beta2, (float)(1.0 / c1),
-                                  (float)(1.0 / c2), (float)prm->eps, (float)prm->lower, c->Abf, c->st));
+    gcp_status s = do_step(c, iter, p, q, prm, t);
+    if (s) return s;
+    if (dloss_out)
+        GCP_CUDA(c, cudaMemcpyAsync(dloss_out, c->dloss, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     return GCP_OK;
 }
 
@@ -690,8 +762,7 @@ gcp_status gcp_fit(gcp_ctx *c, const gcp_fit_params *prm, gcp_fit_report *rep) {
     if ((s = backup(true))) return s;
     for (int epoch = 0; epoch < prm->max_epochs; ++epoch) {
         for (int it = 0; it < prm->iters; ++it) {
-            if ((s = run_fused(c, iter++, prm->p, prm->q, true, nullptr))) return s;
-            if ((s = gcp_adam_step(c, &adam, t + 1))) return s;
+            if ((s = do_step(c, iter++, prm->p, prm->q, &adam, t + 1))) return s;
             ++t;
             ++steps_run;
         }

@@ -55,6 +55,22 @@ struct FusedSpec {
 // accumulated in this many global replicas, then folded into G.
 constexpr int kReplicas = 64;
 
+// The epilogue of one training step (gcp_step): loss finish, replica fold,
+// Adam and gradient clearing in one launch.
+struct PostSpec {
+    int64_t n;                      // total_rows * Rp
+    int Rp, R, Htot;
+    float *G, *Grep, *A, *B, *C;
+    void *Abf;
+    const int *hot_slot;
+    float lr, beta1, beta2, c1inv, c2inv, eps, lower;
+    const double *partials;
+    int nblocks;
+    double w_nz, w_z;
+    double *dloss;
+    int *status;
+};
+
 struct LaunchCfg {
     int blocks;
     int threads;
@@ -79,6 +95,7 @@ cudaError_t launch_adam(int64_t n, int Rp, int R, float *A, float *B, float *C, 
                         float beta1, float beta2, float c1inv, float c2inv, float eps, float lower,
                         void *Abf, cudaStream_t st);
 cudaError_t launch_to_bf16(int64_t n, const float *A, void *Abf, cudaStream_t st);
+cudaError_t launch_post_step(const PostSpec &p, cudaStream_t st);
 int fused_max_blocks(int d, bool bf16, int cols);
 
 }  // namespace gcpk
@@ -117,6 +134,7 @@ struct gcp_ctx {
     double *h_loss = nullptr;     // pinned mirror of dloss
 
     // hot-row replicas of the gradient
+    bool g_clear = true;          // G is all zero (gcp_step leaves it so)
     int *hot_slot = nullptr;      // [total_rows] row -> replica slot or -1
     int *hot_row = nullptr;       // [Htot] slot -> row
     int small_base[GCP_MAX_NDIM] = {0};

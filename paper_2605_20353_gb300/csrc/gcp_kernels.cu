@@ -24,6 +24,8 @@ namespace gcpk {
 
 constexpr int kThreads = 256;
 
+static int elementwise_blocks(int64_t n);
+
 struct RowOffsets {
     int64_t off[GCP_MAX_NDIM];
 };
@@ -460,6 +462,63 @@ __global__ void k_adam(int64_t n, int Rp, int R, float *__restrict__ A, float *_
         A[e] = a;
         if (Abf) Abf[e] = __float2bfloat16_rn(a);
     }
+}
+
+// One training step's epilogue after the fused pass, in one launch: block 0
+// first finishes the FP64 loss from the block partials (fixed order); then
+// every element of the flat parameter vector takes its gradient (adding the
+// replicas of a hot row and clearing them), applies Algorithm 1, and clears
+// G for the next step.
+__global__ void __launch_bounds__(kThreads) k_post_step(PostSpec P) {
+    if (blockIdx.x == 0) {
+        __shared__ double sh[3][kThreads];
+        double t[3] = {0.0, 0.0, 0.0};
+        for (int b = threadIdx.x; b < P.nblocks; b += kThreads)
+            for (int c = 0; c < 3; ++c) t[c] += P.partials[4 * b + c];
+        for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] = t[c];
+        __syncthreads();
+        for (int w = kThreads / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w)
+                for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double loss = P.w_nz * sh[0][0] + P.w_z * sh[1][0];
+            P.dloss[0] = loss;
+            P.dloss[1] = sh[2][0];
+            if (!isfinite(loss)) atomicOr(P.status, kErrNonfinite);
+        }
+    }
+    const int64_t plane = (int64_t)P.Htot * P.Rp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < P.n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int row = (int)(e / P.Rp), col = (int)(e % P.Rp);
+        float g = P.G[e];
+        const int hs = P.hot_slot ? __ldg(P.hot_slot + row) : -1;
+        if (hs >= 0) {
+            float v[kReplicas];
+            const int64_t o = (int64_t)hs * P.Rp + col;
+#pragma unroll
+            for (int r = 0; r < kReplicas; ++r) v[r] = P.Grep[r * plane + o];
+#pragma unroll
+            for (int r = 0; r < kReplicas; ++r) g += v[r];
+#pragma unroll
+            for (int r = 0; r < kReplicas; ++r) P.Grep[r * plane + o] = 0.0f;
+        }
+        P.G[e] = 0.0f;
+        if (col >= P.R) continue;
+        const float b = P.beta1 * P.B[e] + (1.0f - P.beta1) * g;
+        const float c = P.beta2 * P.C[e] + (1.0f - P.beta2) * g * g;
+        P.B[e] = b;
+        P.C[e] = c;
+        const float a = fmaxf(P.A[e] - P.lr * ((b * P.c1inv) / sqrtf(c * P.c2inv + P.eps)), P.lower);
+        P.A[e] = a;
+        if (P.Abf) static_cast<__nv_bfloat16 *>(P.Abf)[e] = __float2bfloat16_rn(a);
+    }
+}
+
+cudaError_t launch_post_step(const PostSpec &p, cudaStream_t st) {
+    k_post_step<<<elementwise_blocks(p.n), kThreads, 0, st>>>(p);
+    return cudaGetLastError();
 }
 
 __global__ void k_to_bf16(int64_t n, const float *__restrict__ A, __nv_bfloat16 *Abf) {

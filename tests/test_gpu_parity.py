@@ -432,3 +432,39 @@ def test_nonfused_mttkrp_matches_oracle_and_fused(env, sampling, dtype):
     for n, (a, b) in enumerate(zip(split(G, dims, 32), Go)):
         assert rel_err(a, b) <= TOL_FP32, n
     assert rel_err(G, res["atomic"][1]) <= TOL_FP32
+
+
+# ----------------------------------------------------------- fused step
+@pytest.mark.parametrize("dtype", ["fp32", "bf16"])
+def test_step_equals_grad_then_adam_and_oracle(env, dtype):
+    """gcp_step (fused pass + one epilogue: loss, replica fold, Adam, G
+    cleared) over several steps equals gcp_grad + gcp_adam_step, and the
+    first step equals the oracle's gradient + Adam."""
+    gcp, torch = env
+    w = synth.workload_zipf_count(scale=0.01)
+    dims, p = w["dims"], 9000
+    adam = gcp.AdamParams(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, lower=0.0)
+    a = gcp.gcp_create(dims, w["coords"], w["vals"], 32, "poisson", dtype=dtype, seed=51)
+    b = gcp.gcp_create(dims, w["coords"], w["vals"], 32, "poisson", dtype=dtype, seed=51)
+    a.set_factors(w["factors"])
+    b.set_factors(w["factors"])
+    dl = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for t in range(1, 4):
+        a.step(t, p, p, adam, t, dloss=dl)
+        L, _ = b.grad(t, p, p)
+        b.adam_step(adam, t)
+        a.sync()
+        assert dl.item() == L
+        if t == 1:
+            fac = [bf16_round(x) for x in w["factors"]] if dtype == "bf16" else w["factors"]
+            idx, x, wt, _ = oracle.stratified_samples(51, 1, p, p, dims, w["coords"], w["vals"])
+            _, Go = oracle.sampled_loss_grad(dims, fac, "poisson", idx, x, wt)
+            A = oracle.flat_factors(w["factors"])
+            oracle.adam_step(A, np.zeros_like(A), np.zeros_like(A), np.concatenate([g.ravel() for g in Go]),
+                             1e-3, 0.9, 0.999, 1e-8, 0.0, 1)
+            assert rel_err(np.concatenate([f.ravel() for f in a.get_factors()]), A) <= TOL_FP32
+    fa = np.concatenate([f.ravel() for f in a.get_factors()])
+    fb = np.concatenate([f.ravel() for f in b.get_factors()])
+    assert rel_err(fa, fb) <= TOL_FP32
+    a.close()
+    b.close()
