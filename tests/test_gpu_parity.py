@@ -454,7 +454,10 @@ def test_step_equals_grad_then_adam_and_oracle(env, dtype):
         L, _ = b.grad(t, p, p)
         b.adam_step(adam, t)
         a.sync()
-        assert dl.item() == L
+        if t == 1:  # identical factors: the same fused pass and loss reduction
+            assert dl.item() == L
+        else:  # the factors differ by the atomic summation order of earlier gradients
+            assert dl.item() == pytest.approx(L, rel=1e-9)
         if t == 1:
             fac = [bf16_round(x) for x in w["factors"]] if dtype == "bf16" else w["factors"]
             idx, x, wt, _ = oracle.stratified_samples(51, 1, p, p, dims, w["coords"], w["vals"])
