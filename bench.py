@@ -340,6 +340,19 @@ def fused_vs_nonfused_variant(gcp, torch, stream, launches=10):
     return res
 
 
+def combine_ranks(seconds, units_per_rank, world, dist=None, device="cpu"):
+    """Whole-job throughput of N independent replicas: every rank processed
+    units_per_rank units; the job took as long as its slowest rank (max over
+    ranks of the local timed seconds).  Returns (units per second, max s)."""
+    import torch
+
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    slowest = float(t.item())
+    return world * units_per_rank / slowest, slowest
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -413,12 +426,9 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         ms, kernel_ms, launches = timed_loop(ctx, args.steps, args.warmup, profile=True)
     clocks = clk.summary()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    value, slowest_s = combine_ranks(ms / 1e3, S * args.steps, world, dist, device="cuda")
+    ms = slowest_s * 1e3
     ms_per_step = ms / args.steps
-    value = world * S * args.steps / (ms / 1e3)
 
     # end to end through the public API with host buffers: factors in from
     # pinned host memory, gradient and loss back to the host every step
@@ -439,10 +449,7 @@ def run_ours(args):
         ctx.adam_step(adam, i + 1)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * S * n_e2e / float(e2e_t.item())
+    e2e_value, _ = combine_ranks(e2e_s, S * n_e2e, world, dist, device="cuda")
     ctx.close()
 
     # BF16 factor storage, same workload
