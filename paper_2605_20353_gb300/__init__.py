@@ -155,6 +155,21 @@ class AdamParams:
         return gcp_adam_params(self.lr, self.beta1, self.beta2, self.eps, self.lower)
 
 
+# Hyperparameter presets for gcp_fit (Alg. 2) and the FedAdam server step
+# (Alg. 4): the default column of the paper's parameter-range table and the
+# values its Latin-hypercube study tuned on synthetic count data (Sec. 5.2,
+# tuned-parameter table).  The lower bound 0 keeps count-data factors
+# nonnegative.
+FIT_PRESETS = {
+    "paper_default": dict(adam=AdamParams(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, lower=0.0), decay=0.1),
+    "gcp_sgd_tuned": dict(adam=AdamParams(lr=0.035817, beta1=0.630219, beta2=0.966996, eps=1.388768e-13, lower=0.0),
+                          decay=0.123013),
+    "gcp_fedadam_tuned": dict(adam=AdamParams(lr=0.002185, beta1=0.603286, beta2=0.991181, eps=5.523877e-14,
+                                              lower=0.0),
+                              decay=0.000148, meta_rate=0.029976),
+}
+
+
 class GcpContext:
     """Owns one gcp_ctx (a sparse or dense tensor plus model, gradient and
     Adam state on the GPU)."""

@@ -92,3 +92,14 @@ def test_host_argument_checks_need_no_gpu(lib_path):
     assert lib.gcp_create(3, dims.ctypes.data, 2, coords.ctypes.data, nan.ctypes.data, 4, 0, None,
                           ctypes.byref(h)) == 1
     assert h.value is None
+
+
+def test_fit_presets_are_valid_adam_settings():
+    import paper_2605_20353_gb300 as gcp
+
+    for name, p in gcp.FIT_PRESETS.items():
+        a = p["adam"]
+        assert a.lr > 0 and 0 <= a.beta1 < 1 and 0 <= a.beta2 < 1 and a.eps >= 0, name
+        assert 0 < p["decay"] < 1, name
+    assert gcp.FIT_PRESETS["gcp_sgd_tuned"]["adam"].lr == 0.035817
+    assert gcp.FIT_PRESETS["gcp_fedadam_tuned"]["meta_rate"] == 0.029976

@@ -471,3 +471,21 @@ def test_step_equals_grad_then_adam_and_oracle(env, dtype):
     assert rel_err(fa, fb) <= TOL_FP32
     a.close()
     b.close()
+
+
+def test_fit_with_tuned_preset_on_count_data(env):
+    """gcp_fit with the paper's tuned GCP-SGD hyperparameters on a Poisson
+    count tensor: the objective estimate falls, at most max_fails epochs
+    fail, and the reported objective is the best epoch's."""
+    gcp, torch = env
+    dims = [60, 50, 40]
+    coords, vals = synth.uniform_sparse(dims, 6000, 81, lam=3.0)
+    ctx = gcp.gcp_create(dims, coords, vals, 8, "poisson", seed=82)
+    ctx.set_factors(synth.factors_uniform(dims, 8, 83, lo=0.1, hi=1.0))
+    pre = gcp.FIT_PRESETS["gcp_sgd_tuned"]
+    rep = ctx.fit(pre["adam"], 2000, 2000, 20000, 20000, iters=50, max_epochs=30, max_fails=3, decay=pre["decay"])
+    assert rep["objective"] < rep["objective0"]
+    assert rep["fails"] <= 3 and rep["epochs"] <= 30
+    assert rep["objective"] == min(rep["trace"] + [rep["objective0"]])
+    assert min(f for a in ctx.get_factors() for f in a.ravel()) >= 0.0  # lower bound 0
+    ctx.close()
