@@ -353,6 +353,74 @@ def combine_ranks(seconds, units_per_rank, world, dist=None, device="cpu"):
     return world * units_per_rank / slowest, slowest
 
 
+def bernoulli_variant(gcp, torch, stream, launches=10):
+    """10000 x 10000 x 1000 binary tensor with 2e7 ones from a rank-16
+    logistic generator, Bernoulli-logit loss, rank 64, 2^21 ones + 2^21
+    zeros: gradient time with FP32 / BF16 factors and atomic /
+    deterministic MTTKRP."""
+    import synth
+
+    dims = [10000, 10000, 1000]
+
+    def gen():
+        coords, vals = synth.bernoulli_logit_sparse(dims, 20_000_000, 1004, rank=16)
+        return dict(coords=coords, vals=vals)
+
+    w = synth.cached("bernoulli_full_cv", gen)
+    fac = synth.factors_normal(dims, 64, 2004, std=0.5)
+    S = 1 << 21
+    res = {"workload": "10000x10000x1000, 2e7 ones, Bernoulli-logit, rank 64, p=q=2^21"}
+    for name, dtype, mttkrp in (("fp32_atomic", "fp32", "atomic"), ("bf16_atomic", "bf16", "atomic"),
+                                ("fp32_deterministic", "fp32", "deterministic")):
+        ctx = gcp.gcp_create(dims, w["coords"], w["vals"], 64, "bernoulli", dtype=dtype, mttkrp=mttkrp, seed=7,
+                             stream=stream)
+        ctx.set_factors(fac)
+        ctx.grad_async(0, S, S)
+        ctx.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(launches):
+            ctx.grad_async(1 + i, S, S)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / launches
+        res[name] = {"gradient_ms": ms, "samples_per_s": 2 * S / (ms / 1e3)}
+        ctx.close()
+    return res
+
+
+def autograd_variant(gcp, torch, stream, steps=10):
+    """Dense 100x100x100x20x50 FP32 tensor (rank-8 sinusoidal CP signal +
+    N(0, 0.1^2) noise), Gaussian loss, rank 16, 2^22 uniform samples:
+    forward (sampled loss) + backward (fused MTTKRP adjoint) through the
+    autograd function."""
+    import synth
+    from paper_2605_20353_gb300 import autograd
+
+    dims = [100, 100, 100, 20, 50]
+    X = synth.dense_cp_sinusoid(dims, 1003, rank_true=8, sigma=0.1)
+    ctx = gcp.gcp_create_dense(dims, X, 16, "gaussian", seed=3003, stream=stream)
+    del X
+    A = [torch.tensor(a, device="cuda", requires_grad=True) for a in synth.factors_normal(dims, 16, 2003, std=0.5)]
+    s = 1 << 22
+    loss = autograd.sampled_loss(ctx, 0, s, 0, A)
+    loss.backward()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        for a in A:
+            a.grad = None
+        loss = autograd.sampled_loss(ctx, 1 + i, s, 0, A)
+        loss.backward()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ctx.close()
+    return {"workload": "dense 100x100x100x20x50, Gaussian, rank 16, 2^22 uniform samples",
+            "forward_backward_ms": ms, "samples_per_s": s / (ms / 1e3)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -491,6 +559,8 @@ def run_ours(args):
         line["variants"]["batched_clients"] = batched_variant(gcp, torch, stream)
         line["variants"]["hbm_resident_factors"] = hbm_resident_variant(gcp, torch, stream)
         line["variants"]["fused_vs_nonfused"] = fused_vs_nonfused_variant(gcp, torch, stream)
+        line["variants"]["bernoulli_binary"] = bernoulli_variant(gcp, torch, stream)
+        line["variants"]["autograd_dense"] = autograd_variant(gcp, torch, stream)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
