@@ -489,3 +489,31 @@ def test_fit_with_tuned_preset_on_count_data(env):
     assert rep["objective"] == min(rep["trace"] + [rep["objective0"]])
     assert min(f for a in ctx.get_factors() for f in a.ravel()) >= 0.0  # lower bound 0
     ctx.close()
+
+
+def test_small_gaussian_hundred_epochs_gradient_parity_along_the_fit(env):
+    """50x40x30 Gaussian workload, Adam lr 1e-2 for 100 epochs of 100 steps:
+    the trajectory is chaotic across precisions, so parity is checked per
+    state -- the GPU gradient at the GPU's own factors after 0, 50 and 99
+    epochs against the oracle's gradient at those factors."""
+    gcp, torch = env
+    w = synth.workload_small_gaussian()
+    dims = w["dims"]
+    ctx = gcp.gcp_create(dims, w["coords"], w["vals"], 4, "gaussian", seed=3001)
+    ctx.set_factors(w["factors"])
+    adam = gcp.AdamParams(lr=1e-2)
+    F_start = None
+    for epochs in (0, 50, 49):
+        if epochs:
+            rep = ctx.fit(adam, 1000, 1000, 10000, 10000, iters=100, max_epochs=epochs, max_fails=100, decay=0.5,
+                          iter0=10_000 * (epochs + 1))
+            F_start = F_start or rep["objective0"]
+        fac = ctx.get_factors()
+        L, G = gpu_grad(gcp, torch, ctx, 77, 1000, 1000)
+        idx, x, wt, _ = oracle.stratified_samples(3001, 77, 1000, 1000, dims, w["coords"], w["vals"])
+        Lo, Go = oracle.sampled_loss_grad(dims, fac, "gaussian", idx, x, wt)
+        assert abs(L - Lo) <= TOL_FP32 * abs(Lo)
+        for n, (a, b) in enumerate(zip(split(G, dims, 4), Go)):
+            assert rel_err(a, b) <= TOL_FP32, (epochs, n)
+    assert rep["objective"] < F_start
+    ctx.close()
