@@ -517,3 +517,24 @@ def test_small_gaussian_hundred_epochs_gradient_parity_along_the_fit(env):
             assert rel_err(a, b) <= TOL_FP32, (epochs, n)
     assert rep["objective"] < F_start
     ctx.close()
+
+
+def test_fit_restores_state_after_failed_epochs(env):
+    """An epoch that does not lower the objective estimate is undone (factors
+    and moments restored exactly) and the rate decays; the fit stops after
+    max_fails such epochs."""
+    gcp, torch = env
+    dims = [40, 30, 20]
+    coords, vals = synth.uniform_sparse(dims, 1500, 91, lam=2.0)
+    F0 = synth.factors_uniform(dims, 6, 92, lo=0.1, hi=1.0)
+    ctx = gcp.gcp_create(dims, coords, vals, 6, "poisson", seed=93)
+    ctx.set_factors(F0)
+    # a rate this large with lower bound 0 drives factors to the bound: every epoch fails
+    rep = ctx.fit(gcp.AdamParams(lr=50.0, lower=0.0), 500, 500, 4000, 4000, iters=20, max_epochs=10, max_fails=3,
+                  decay=0.5)
+    assert rep["fails"] == 3 and rep["epochs"] == 3 and rep["iterations"] == 0
+    assert rep["objective"] == rep["objective0"]
+    assert rep["lr"] == pytest.approx(50.0 * 0.5 ** 3)
+    for a, b in zip(ctx.get_factors(), F0):
+        assert np.array_equal(a, b)
+    ctx.close()
