@@ -10,7 +10,7 @@
 //   2. per mode n, a stable LSD radix sort (8-bit digits) orders the sample
 //      ids by row i_n, ties in sample order;
 //   3. a chunked segmented reduction walks the sorted list in chunks of kChunk
-//      positions, one chunk per group of lanes, recomputing the Khatri-Rao row
+//      (64) positions, one chunk per group of lanes, recomputing the Khatri-Rao row
 //      products.  A run of equal rows that lies inside one chunk is stored to
 //      G directly; a run that crosses a chunk edge leaves a partial vector,
 //      and the partials (again sorted by row) are reduced the same way, level
@@ -30,7 +30,8 @@ namespace {
 
 constexpr int kT = 256;            // threads per block
 constexpr int kTile = 4096;        // keys per radix-sort block
-constexpr int kChunk = 256;        // sorted positions per segmented-reduction chunk
+constexpr int kChunk = 64;         // sorted positions per segmented-reduction chunk
+constexpr int kScanBlock = 2048;   // elements per block of the multi-block scan
 
 // --------------------------------------------------------------- radix sort
 __global__ void k_radix_hist(const int32_t *__restrict__ keys, int key_stride, int64_t n, int shift,
@@ -45,8 +46,43 @@ __global__ void k_radix_hist(const int32_t *__restrict__ keys, int key_stride, i
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive prefix sum of n ints in place (one block, fixed order).
-__global__ void k_scan_exclusive(int32_t *a, int64_t n, int32_t *total) {
+// Exclusive prefix sum of n ints in place, in three phases: each block of
+// kScanBlock elements scans itself and records its total; one block scans
+// the totals (and writes the grand total); each block adds its offset.
+__global__ void k_scan_blocks(int32_t *a, int64_t n, int32_t *block_sums) {
+    __shared__ int32_t warp_tot[kT / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * (kScanBlock / kT);
+    int32_t v[kScanBlock / kT];
+    int32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanBlock / kT; ++j) {
+        v[j] = base + j < n ? a[base + j] : 0;
+        sum += v[j];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t incl = sum;  // inclusive scan of the thread sums within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    int32_t before = 0, block_total = 0;
+    for (int w = 0; w < kT / 32; ++w) {
+        if (w < warp) before += warp_tot[w];
+        block_total += warp_tot[w];
+    }
+    int32_t run = before + incl - sum;
+#pragma unroll
+    for (int j = 0; j < kScanBlock / kT; ++j) {
+        if (base + j < n) a[base + j] = run;
+        run += v[j];
+    }
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = block_total;
+}
+
+__global__ void k_scan_top(int32_t *a, int64_t n, int32_t *total) {
     __shared__ int64_t part[kT];
     const int64_t per = (n + kT - 1) / kT;
     const int64_t lo = (int64_t)threadIdx.x * per, hi = lo + per < n ? lo + per : n;
@@ -70,6 +106,19 @@ __global__ void k_scan_exclusive(int32_t *a, int64_t n, int32_t *total) {
         a[i] = (int32_t)run;
         run += v;
     }
+}
+
+__global__ void k_scan_add(int32_t *a, int64_t n, const int32_t *block_sums) {
+    const int32_t off = block_sums[blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    for (int j = threadIdx.x; j < kScanBlock && base + j < n; j += kT) a[base + j] += off;
+}
+
+void scan_exclusive(int32_t *a, int64_t n, int32_t *total, int32_t *block_sums, cudaStream_t st) {
+    const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    k_scan_blocks<<<(unsigned)nb, kT, 0, st>>>(a, n, block_sums);
+    k_scan_top<<<1, kT, 0, st>>>(block_sums, nb, total);
+    k_scan_add<<<(unsigned)nb, kT, 0, st>>>(a, n, block_sums);
 }
 
 // Stable scatter of one 8-bit digit pass.  Keys of a tile are ranked in
@@ -207,14 +256,15 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
 // Levels 2+: sorted (key, partial vector) list -> G rows and edge carries.
 template <int COLS>
 __global__ void __launch_bounds__(kT) k_seg_vectors(const SegSpec P, const int32_t *__restrict__ keys,
-                                                    const float *__restrict__ vecs, int64_t n, int32_t *ckey,
-                                                    float *cvec) {
+                                                    const float *__restrict__ vecs, const int32_t *__restrict__ dn,
+                                                    int32_t *ckey, float *cvec) {
     constexpr int NQ = COLS / 4;
     const int lane = threadIdx.x & 31;
     const int L = 1 << P.log2L;
     const int glane = lane & (L - 1);
     const int64_t group = ((int64_t)blockIdx.x * kT + threadIdx.x) >> P.log2L;
     const int64_t ngroups = ((int64_t)gridDim.x * kT) >> P.log2L;
+    const int64_t n = *dn;  // list length, written on the device by the compaction
     const int64_t nchunks = (n + kChunk - 1) / kChunk;
     int col[NQ];
 #pragma unroll
@@ -309,6 +359,8 @@ static gcp_status det_scratch(gcp_ctx *c, int64_t S, size_t *offs) {
     offs[12] = take((size_t)2 * nchunk * 4);        // compacted keys
     offs[13] = take((size_t)2 * nchunk * c->Rp * 4);
     offs[14] = take(16);                            // list length
+    const int64_t scan_n = 256 * ntiles > 2 * nchunk ? 256 * ntiles : 2 * nchunk;
+    offs[15] = take((size_t)((scan_n + kScanBlock - 1) / kScanBlock + 1) * 4);  // scan block sums
     if (o > c->det_scratch_bytes) {
         cudaFree(c->det_scratch);
         c->det_scratch = nullptr;
@@ -343,7 +395,7 @@ static void launch_seg_samples(const SegSpec &P, int cols, int grid, const int32
 
 gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     const int64_t S = f0.s.p + f0.s.q;
-    size_t offs[15];
+    size_t offs[16];
     gcp_status s = det_scratch(c, S > 0 ? S : 1, offs);
     if (s) return s;
     char *base = static_cast<char *>(c->det_scratch);
@@ -360,6 +412,7 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     int32_t *lkey = reinterpret_cast<int32_t *>(base + offs[12]);
     float *lvec = reinterpret_cast<float *>(base + offs[13]);
     int32_t *dlen = reinterpret_cast<int32_t *>(base + offs[14]);
+    int32_t *bsum = reinterpret_cast<int32_t *>(base + offs[15]);
     cudaStream_t st = c->st;
 
     // 1. loss partials and the materialised gradient tensor
@@ -393,7 +446,7 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
         int32_t *kout = kA, *vout = vA;
         for (int shift = 0; shift < bits; shift += 8) {
             k_radix_hist<<<(int)ntiles, kT, 0, st>>>(kin, kstride, S, shift, hist, (int)ntiles);
-            k_scan_exclusive<<<1, kT, 0, st>>>(hist, 256 * ntiles, nullptr);
+            scan_exclusive(hist, 256 * ntiles, nullptr, bsum, st);
             k_radix_scatter<<<(int)ntiles, kT, 0, st>>>(kin, kstride, vin, S, shift, hist, (int)ntiles, kout, vout);
             DET_CUDA(cudaGetLastError());
             kin = kout;
@@ -411,26 +464,24 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
         else
             launch_seg_samples<float>(P, c->cols, grid, kin, vin, S, ckey_out, cvec_out, st);
         DET_CUDA(cudaGetLastError());
-        // levels 2+: compact the carries and reduce them again
+        // levels 2+: compact the carries and reduce them again.  The list
+        // length stays on the device; grids are sized by its upper bound
+        // (two carries per chunk of the previous level), so no host sync.
         int64_t nslots = 2 * nch;
         while (nch > 1) {
             k_carry_flags<<<grid_for(nslots, kT), kT, 0, st>>>(ckey_out, nslots, cpos);
-            k_scan_exclusive<<<1, kT, 0, st>>>(cpos, nslots, dlen);
+            scan_exclusive(cpos, nslots, dlen, bsum, st);
             k_carry_compact<<<grid_for(nslots * c->Rp, kT), kT, 0, st>>>(ckey_out, cvec_out, nslots, cpos, c->Rp,
                                                                          lkey, lvec);
-            int32_t len = 0;
-            DET_CUDA(cudaMemcpyAsync(&len, dlen, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-            DET_CUDA(cudaStreamSynchronize(st));
-            if (len == 0) break;
-            nch = (len + kChunk - 1) / kChunk;
+            nch = (nslots + kChunk - 1) / kChunk;
             nslots = 2 * nch;
             std::swap(ckey_in, ckey_out);
             std::swap(cvec_in, cvec_out);
             k_fill_int<<<grid_for(nslots, kT), kT, 0, st>>>(ckey_out, nslots, -1);
             if (c->cols == 8)
-                k_seg_vectors<8><<<grid_for(nch * lanes, kT), kT, 0, st>>>(P, lkey, lvec, len, ckey_out, cvec_out);
+                k_seg_vectors<8><<<grid_for(nch * lanes, kT), kT, 0, st>>>(P, lkey, lvec, dlen, ckey_out, cvec_out);
             else
-                k_seg_vectors<4><<<grid_for(nch * lanes, kT), kT, 0, st>>>(P, lkey, lvec, len, ckey_out, cvec_out);
+                k_seg_vectors<4><<<grid_for(nch * lanes, kT), kT, 0, st>>>(P, lkey, lvec, dlen, ckey_out, cvec_out);
             DET_CUDA(cudaGetLastError());
         }
     }
