@@ -28,7 +28,7 @@ def lib_path():
     return build.build()
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_core_calls():
     names = _declared()
     for n in ["gcp_create", "gcp_sample", "gcp_loss", "gcp_grad", "gcp_adam_step", "gcp_fit"]:
         assert n in names
