@@ -32,6 +32,7 @@ constexpr int kT = 256;            // threads per block
 constexpr int kTile = 4096;        // keys per radix-sort block
 constexpr int kChunk = 64;         // sorted positions per segmented-reduction chunk
 constexpr int kScanBlock = 2048;   // elements per block of the multi-block scan
+constexpr int kAhead = 4;          // carry vectors fetched ahead in the reduction of levels 2+
 
 // --------------------------------------------------------------- radix sort
 __global__ void k_radix_hist(const int32_t *__restrict__ keys, int key_stride, int64_t n, int shift,
@@ -167,6 +168,7 @@ __global__ void k_radix_scatter(const int32_t *__restrict__ keys, int key_stride
 // ------------------------------------------------------ segmented reduction
 struct SegSpec {
     int n_mode;        // mode whose gradient rows are reduced
+    int rown;          // its first row in G
     int d, Rp, cols, log2L;
     int rowoff[GCP_MAX_NDIM];
     const void *F;     // factors read by the kernels (FP32 or BF16)
@@ -202,54 +204,98 @@ __device__ __forceinline__ void emit_run(float *G, int Rp, int row_base, int key
 }
 
 // Level 1: sorted sample ids of one mode -> G rows and edge carries.
-template <typename TF, int COLS>
+// The group walks its chunk in batches of L positions.  Each lane first
+// fetches one position's metadata (row key, y_s and the factor-row offsets
+// of the sample's cell), so the dependent id -> sample lookups of a batch
+// overlap; the positions are then taken in order, their metadata broadcast
+// by shuffles and the factor rows of U positions gathered before any of
+// them is accumulated.  Products and sums keep the sequential order.
+template <typename TF, int COLS, int D>
 __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32_t *__restrict__ keys,
                                                     const int32_t *__restrict__ ids, int64_t n, int32_t *ckey,
                                                     float *cvec) {
     constexpr int NQ = COLS / 4;
+    constexpr int U0 = 32 / ((D - 1) * COLS);
+    constexpr int U = U0 < 1 ? 1 : (U0 > 4 ? 4 : U0);  // positions gathered ahead
     const int lane = threadIdx.x & 31;
     const int L = 1 << P.log2L;
     const int glane = lane & (L - 1);
+    const unsigned gmask = (L == 32) ? 0xFFFFFFFFu : (((1u << L) - 1u) << (lane & ~(L - 1)));
     const int64_t group = ((int64_t)blockIdx.x * kT + threadIdx.x) >> P.log2L;
     const int64_t ngroups = ((int64_t)gridDim.x * kT) >> P.log2L;
     const int64_t nchunks = (n + kChunk - 1) / kChunk;
-    const TF *F = static_cast<const TF *>(P.F);
+    const int nm = P.n_mode;
+    const TF *__restrict__ F = static_cast<const TF *>(P.F);
+    const float *__restrict__ Yval = P.Yval;
+    const int32_t *__restrict__ Ycoord = P.Ycoord;
     int col[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) col[q] = q * (P.Rp >> 1) + 4 * glane;
+    int roff[D - 1];  // first rows of the other modes (constant indices only)
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) roff[j] = j < nm ? P.rowoff[j] : P.rowoff[j + 1];
+    const int rown = P.rown;
     for (int64_t c = group; c < nchunks; c += ngroups) {
         const int64_t lo = c * kChunk, hi = lo + kChunk < n ? lo + kChunk : n;
+        const int len = (int)(hi - lo);
         float acc[COLS];
 #pragma unroll
         for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
         int cur = keys[lo];
         bool before = lo > 0 && keys[lo - 1] == cur;
-        for (int64_t i = lo; i < hi; ++i) {
-            const int key = keys[i];
-            if (key != cur) {
-                emit_run<NQ>(P.G, P.Rp, P.rowoff[P.n_mode], cur, acc, col, before, false, (int)c, ckey, cvec);
+        for (int b = 0; b < len; b += L) {
+            // this lane's position of the batch: key, y and the D-1 row
+            // offsets of the other modes (mode k < n at j = k, k > n at k-1)
+            const int64_t pi = lo + b + glane;
+            int mkey = 0, moff[D - 1];
+            float my = 0.0f;
 #pragma unroll
-                for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
-                cur = key;
-                before = false;
+            for (int j = 0; j < D - 1; ++j) moff[j] = 0;
+            if (pi < hi) {
+                mkey = keys[pi];
+                const int64_t s = ids[pi];
+                my = Yval[s];
+#pragma unroll
+                for (int j = 0; j < D - 1; ++j)
+                    moff[j] = (roff[j] + Ycoord[s * D + (j < nm ? j : j + 1)]) * P.Rp;
             }
-            const int s = ids[i];
-            const float y = P.Yval[s];
-            float prod[COLS];
+            const int nb = len - b < L ? len - b : L;
+            for (int t0 = 0; t0 < nb; t0 += U) {
+                int key[U];
+                float y[U], a[U][D - 1][COLS];
 #pragma unroll
-            for (int v = 0; v < COLS; ++v) prod[v] = y;
-            for (int k = 0; k < P.d; ++k) {
-                if (k == P.n_mode) continue;
-                float a[COLS];
-                load_cols<TF, NQ>(F, (P.rowoff[k] + P.Ycoord[(int64_t)s * P.d + k]) * P.Rp, col, a);
+                for (int u = 0; u < U; ++u) {
+                    const int t = t0 + u < nb ? t0 + u : nb - 1;  // group-uniform
+                    key[u] = __shfl_sync(gmask, mkey, t, L);
+                    y[u] = __shfl_sync(gmask, my, t, L);
 #pragma unroll
-                for (int v = 0; v < COLS; ++v) prod[v] *= a[v];
+                    for (int j = 0; j < D - 1; ++j)
+                        load_cols<TF, NQ>(F, __shfl_sync(gmask, moff[j], t, L), col, a[u][j]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (t0 + u >= nb) break;
+                    if (key[u] != cur) {
+                        emit_run<NQ>(P.G, P.Rp, rown, cur, acc, col, before, false, (int)c, ckey, cvec);
+#pragma unroll
+                        for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
+                        cur = key[u];
+                        before = false;
+                    }
+                    float prod[COLS];
+#pragma unroll
+                    for (int v = 0; v < COLS; ++v) prod[v] = y[u];
+#pragma unroll
+                    for (int j = 0; j < D - 1; ++j)
+#pragma unroll
+                        for (int v = 0; v < COLS; ++v) prod[v] *= a[u][j][v];
+#pragma unroll
+                    for (int v = 0; v < COLS; ++v) acc[v] += prod[v];
+                }
             }
-#pragma unroll
-            for (int v = 0; v < COLS; ++v) acc[v] += prod[v];
         }
         const bool after = hi < n && keys[hi] == cur;
-        emit_run<NQ>(P.G, P.Rp, P.rowoff[P.n_mode], cur, acc, col, before, after, (int)c, ckey, cvec);
+        emit_run<NQ>(P.G, P.Rp, rown, cur, acc, col, before, after, (int)c, ckey, cvec);
     }
 }
 
@@ -269,6 +315,7 @@ __global__ void __launch_bounds__(kT) k_seg_vectors(const SegSpec P, const int32
     int col[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) col[q] = q * (P.Rp >> 1) + 4 * glane;
+    const int rown = P.rown;
     for (int64_t c = group; c < nchunks; c += ngroups) {
         const int64_t lo = c * kChunk, hi = lo + kChunk < n ? lo + kChunk : n;
         float acc[COLS];
@@ -276,27 +323,38 @@ __global__ void __launch_bounds__(kT) k_seg_vectors(const SegSpec P, const int32
         for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
         int cur = keys[lo];
         bool before = lo > 0 && keys[lo - 1] == cur;
-        for (int64_t i = lo; i < hi; ++i) {
-            const int key = keys[i];
-            if (key != cur) {
-                emit_run<NQ>(P.G, P.Rp, P.rowoff[P.n_mode], cur, acc, col, before, false, (int)c, ckey, cvec);
+        for (int64_t i0 = lo; i0 < hi; i0 += kAhead) {
+            // fetch kAhead positions' keys and vector slices, then add in order
+            int key[kAhead];
+            float4 t[kAhead][NQ];
 #pragma unroll
-                for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
-                cur = key;
-                before = false;
+            for (int u = 0; u < kAhead; ++u) {
+                const int64_t i = i0 + u < hi ? i0 + u : hi - 1;
+                key[u] = keys[i];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) t[u][q] = *reinterpret_cast<const float4 *>(vecs + i * P.Rp + col[q]);
             }
-            const float *vv = vecs + i * P.Rp;
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const float4 t = *reinterpret_cast<const float4 *>(vv + col[q]);
-                acc[4 * q] += t.x;
-                acc[4 * q + 1] += t.y;
-                acc[4 * q + 2] += t.z;
-                acc[4 * q + 3] += t.w;
+            for (int u = 0; u < kAhead; ++u) {
+                if (i0 + u >= hi) break;
+                if (key[u] != cur) {
+                    emit_run<NQ>(P.G, P.Rp, rown, cur, acc, col, before, false, (int)c, ckey, cvec);
+#pragma unroll
+                    for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
+                    cur = key[u];
+                    before = false;
+                }
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    acc[4 * q] += t[u][q].x;
+                    acc[4 * q + 1] += t[u][q].y;
+                    acc[4 * q + 2] += t[u][q].z;
+                    acc[4 * q + 3] += t[u][q].w;
+                }
             }
         }
         const bool after = hi < n && keys[hi] == cur;
-        emit_run<NQ>(P.G, P.Rp, P.rowoff[P.n_mode], cur, acc, col, before, after, (int)c, ckey, cvec);
+        emit_run<NQ>(P.G, P.Rp, rown, cur, acc, col, before, after, (int)c, ckey, cvec);
     }
 }
 
@@ -311,17 +369,20 @@ __global__ void k_carry_flags(const int32_t *ckey, int64_t n, int32_t *flag) {
         flag[i] = ckey[i] >= 0 ? 1 : 0;
 }
 
-// Order-preserving compaction of the used carry slots.
-__global__ void k_carry_compact(const int32_t *ckey, const float *cvec, int64_t n, const int32_t *pos, int Rp,
+// Order-preserving compaction of the used carry slots, one 16-byte quad of
+// a vector per thread (Rp = 4 << log2q).
+__global__ void k_carry_compact(const int32_t *ckey, const float *cvec, int64_t n, const int32_t *pos, int log2q,
                                 int32_t *okey, float *ovec) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * Rp;
+    const int Rp = 4 << log2q;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (n << log2q);
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / Rp;
-        const int c = (int)(e % Rp);
-        if (ckey[i] < 0) continue;
+        const int64_t i = e >> log2q;
+        const int c = 4 * (int)(e & ((1 << log2q) - 1));
+        const int32_t key = ckey[i];
+        if (key < 0) continue;
         const int64_t o = pos[i];
-        ovec[o * Rp + c] = cvec[i * Rp + c];
-        if (c == 0) okey[o] = ckey[i];
+        *reinterpret_cast<float4 *>(ovec + o * Rp + c) = *reinterpret_cast<const float4 *>(cvec + i * Rp + c);
+        if (c == 0) okey[o] = key;
     }
 }
 
@@ -384,13 +445,27 @@ static gcp_status det_scratch(gcp_ctx *c, int64_t S, size_t *offs) {
         }                                                                        \
     } while (0)
 
+template <typename TF, int D>
+static void launch_seg_samples_d(const SegSpec &P, int cols, int grid, const int32_t *keys, const int32_t *ids,
+                                 int64_t n, int32_t *ckey, float *cvec, cudaStream_t st) {
+    if (cols == 8)
+        k_seg_samples<TF, 8, D><<<grid, kT, 0, st>>>(P, keys, ids, n, ckey, cvec);
+    else
+        k_seg_samples<TF, 4, D><<<grid, kT, 0, st>>>(P, keys, ids, n, ckey, cvec);
+}
+
 template <typename TF>
 static void launch_seg_samples(const SegSpec &P, int cols, int grid, const int32_t *keys, const int32_t *ids,
                                int64_t n, int32_t *ckey, float *cvec, cudaStream_t st) {
-    if (cols == 8)
-        k_seg_samples<TF, 8><<<grid, kT, 0, st>>>(P, keys, ids, n, ckey, cvec);
-    else
-        k_seg_samples<TF, 4><<<grid, kT, 0, st>>>(P, keys, ids, n, ckey, cvec);
+    switch (P.d) {
+        case 2: launch_seg_samples_d<TF, 2>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
+        case 3: launch_seg_samples_d<TF, 3>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
+        case 4: launch_seg_samples_d<TF, 4>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
+        case 5: launch_seg_samples_d<TF, 5>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
+        case 6: launch_seg_samples_d<TF, 6>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
+        case 7: launch_seg_samples_d<TF, 7>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
+        default: launch_seg_samples_d<TF, 8>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
+    }
 }
 
 gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
@@ -435,8 +510,11 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     P.Yval = Yval;
     P.G = c->G;
     const int lanes = 1 << c->log2L;
+    int log2q = 0;  // Rp = 4 << log2q (Rp is four times a power of two)
+    while ((4 << log2q) < c->Rp) ++log2q;
     for (int n = 0; n < c->d; ++n) {
         P.n_mode = n;
+        P.rown = (int)c->rowoff[n];
         // 2. stable LSD radix sort of sample ids by row i_n
         int bits = 1;
         while ((1ll << bits) < c->dims[n]) ++bits;
@@ -471,8 +549,8 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
         while (nch > 1) {
             k_carry_flags<<<grid_for(nslots, kT), kT, 0, st>>>(ckey_out, nslots, cpos);
             scan_exclusive(cpos, nslots, dlen, bsum, st);
-            k_carry_compact<<<grid_for(nslots * c->Rp, kT), kT, 0, st>>>(ckey_out, cvec_out, nslots, cpos, c->Rp,
-                                                                         lkey, lvec);
+            k_carry_compact<<<grid_for(nslots * (c->Rp / 4), kT), kT, 0, st>>>(ckey_out, cvec_out, nslots, cpos,
+                                                                               log2q, lkey, lvec);
             nch = (nslots + kChunk - 1) / kChunk;
             nslots = 2 * nch;
             std::swap(ckey_in, ckey_out);
