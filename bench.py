@@ -342,6 +342,35 @@ def fused_vs_nonfused_variant(gcp, torch, stream, launches=10):
     return res
 
 
+def l2_flushed_variant(make, torch, p, q, launches=20):
+    """The benchmark's fused launch timed alone, warm (factors and gradient
+    rows left in L2 by the previous launch, as in training) and cold (L2
+    flushed by writing 512 MiB just before each launch): medians of
+    `launches` fused-kernel times from the library's own CUDA events."""
+    ctx = make("fp32")
+    flush = torch.empty(128 << 20, dtype=torch.float32, device="cuda")
+    for i in range(3):
+        ctx.grad_async(30_000 + i, p, q)
+    ctx.sync()
+    ctx.profile(True)
+    ctx.profile_read()
+    res = {}
+    for mode in ("warm", "cold"):
+        times = []
+        for i in range(launches):
+            if mode == "cold":
+                flush.fill_(float(i))
+            ctx.grad_async(40_000 + i, p, q)
+            ms, n = ctx.profile_read()
+            times.append(ms / max(1, n))
+        res[f"{mode}_ms_median"] = statistics.median(times)
+    ctx.profile(False)
+    ctx.close()
+    res["cold_over_warm"] = res["cold_ms_median"] / res["warm_ms_median"]
+    res["workload"] = "the benchmark launch (2^21 samples); flush = 512 MiB written before each cold launch"
+    return res
+
+
 def combine_ranks(seconds, units_per_rank, world, dist=None, device="cpu"):
     """Whole-job throughput of N independent replicas: every rank processed
     units_per_rank units; the job took as long as its slowest rank (max over
@@ -567,6 +596,7 @@ def run_ours(args):
                                           "kernel_ms_per_launch": kms_bf / max(1, nl_bf),
                                           "achieved_gbs": bps_bf * S / (kms_bf / 1e3 / max(1, nl_bf)) / 1e9}}}
     if not args.no_variants:
+        line["variants"]["l2_warm_vs_flushed"] = l2_flushed_variant(make, torch, p, q)
         line["variants"]["batched_clients"] = batched_variant(gcp, torch, stream)
         line["variants"]["hbm_resident_factors"] = hbm_resident_variant(gcp, torch, stream)
         line["variants"]["fused_vs_nonfused"] = fused_vs_nonfused_variant(gcp, torch, stream)
