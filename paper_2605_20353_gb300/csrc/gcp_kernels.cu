@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
     for (int q = 0; q < NQ; ++q) col[q] = q * (P.Rp >> 1) + 4 * glane;
     const int p = (int)P.s.p;  // sample counts of one call are below 2^31
     const int S = (int)(P.s.p + P.s.q);
-    const int ntiles = (S + 31) >> 5;
+    const int ntiles = (int)(((int64_t)S + 31) >> 5);  // S may be 2^31 - 1
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const TF *__restrict__ F = static_cast<const TF *>(P.F);
@@ -159,9 +159,10 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
     // A1: start the draw of this lane's sample of `tile` into stage `st`;
     // returns the key of a stratified zero candidate (kEmpty otherwise).
     auto issue = [&](int tile, int st) -> uint64_t {
+        if (tile >= ntiles) return kEmpty;
         const int s = (tile << 5) + lane;
         int32_t *slot = s_slot[st][warp][lane];
-        if (tile >= ntiles || s >= S) return kEmpty;
+        if (s >= S) return kEmpty;
         if (uniform) {
             int32_t idx[D];
             draw_tuple<D>(P.s, kStreamUniform, (uint64_t)s, 0, idx);

@@ -291,6 +291,55 @@ def test_exhausted_zero_draw_is_reported(env):
     ctx.close()
 
 
+def test_half_dense_tensor_redraws(env):
+    """Half of the cells are nonzeros, so about every other zero candidate
+    is rejected and redrawn: bit-exact samples, and gradient parity through
+    the fused pass's redraw path."""
+    gcp, torch = env
+    dims = [4, 5, 6]
+    coords, vals, factors = problem(dims, 60, 8, "poisson", 910)
+    ctx = gcp.gcp_create(dims, coords, vals, 8, "poisson", seed=13)
+    idx, x, _ = ctx.sample(5, 3001, 2999)
+    ido, xo, _, _ = oracle.stratified_samples(13, 5, 3001, 2999, dims, coords, vals)
+    assert np.array_equal(idx.cpu().numpy(), ido)
+    assert np.array_equal(x.cpu().numpy(), xo.astype(np.float32))
+    ctx.close()
+    check_grad(gcp, torch, dims, coords, vals, 8, "poisson", factors, 3001, 2999, t=5, seed=13)
+
+
+@pytest.mark.parametrize("dims", [[1, 30, 20], [40, 1, 1, 9]])
+def test_modes_of_size_one(env, dims):
+    """Every sample falls in row 0 of a size-1 mode."""
+    gcp, torch = env
+    coords, vals, factors = problem(dims, int(np.prod(dims)) // 4, 4, "gaussian", 920 + len(dims))
+    check_grad(gcp, torch, dims, coords, vals, 4, "gaussian", factors, 1000, 1003, t=2)
+
+
+def test_largest_sample_count_per_call(env):
+    """p + q = 2^31 - 1, the most one call accepts, on a problem whose
+    sampled loss is known whatever is drawn: rank 1 with all factors 1 gives
+    m = 1 in every cell, and all nonzeros are 1, so a nonzero costs 0, a zero
+    costs (0 - 1)^2 = 1 and the loss is (M - N)/q * q = M - N.  Per-tile sums
+    of ones are exact in FP32 and their total is exact in FP64, so the loss
+    shows that every tile of the largest launch was taken exactly once."""
+    gcp, torch = env
+    dims = [50, 40, 30]
+    M, N = 60000, 2000
+    coords, _ = synth.uniform_sparse(dims, N, 930)
+    ctx = gcp.gcp_create(dims, coords, np.ones(N, np.float32), 1, "gaussian", seed=17)
+    ctx.set_factors([np.ones((I, 1), np.float32) for I in dims])
+    p = 1 << 30
+    q = (1 << 31) - 1 - p
+    L, G = gpu_grad(gcp, torch, ctx, 0, p, q)
+    assert L == pytest.approx(M - N, rel=1e-12)
+    assert np.all(np.isfinite(G))
+    # each zero adds w_z * f' = 2 (M - N) / q to one row per mode; a mode's
+    # rows sum to 2 (M - N), up to FP32 rounding over ~2^30 additions
+    for g in split(G, dims, 1):
+        assert float(g.astype(np.float64).sum()) == pytest.approx(2 * (M - N), rel=0.05)
+    ctx.close()
+
+
 def test_duplicate_nonzeros_rejected(env):
     gcp, torch = env
     coords = np.array([[0, 1, 1], [2, 0, 1], [0, 1, 1]], dtype=np.int32)
