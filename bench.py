@@ -423,8 +423,9 @@ def bernoulli_variant(gcp, torch, stream, launches=10):
 def autograd_variant(gcp, torch, stream, steps=10):
     """Dense 100x100x100x20x50 FP32 tensor (rank-8 sinusoidal CP signal +
     N(0, 0.1^2) noise), Gaussian loss, rank 16, 2^22 uniform samples:
-    forward (sampled loss) + backward (fused MTTKRP adjoint) through the
-    autograd function."""
+    forward (sampled loss and, in the same fused pass, the gradient) +
+    backward (the gradient scaled by the incoming one) through the autograd
+    function."""
     import synth
     from paper_2605_20353_gb300 import autograd
 

@@ -220,6 +220,14 @@ gcp_status gcp_grad(gcp_ctx *ctx, uint64_t iter, int64_t p, int64_t q, float *G_
 gcp_status gcp_grad_async(gcp_ctx *ctx, uint64_t iter, int64_t p, int64_t q, const float *dscale,
                           float *G_out, double *dloss_out);
 
+/* y[i] = dscale[0] * x[i] for i < n, on the context's stream.  dscale, x
+ * and y are device pointers (y may equal x); nothing is allocated.  The
+ * paper has no counterpart: the autograd binding computes the loss and the
+ * gradient in one fused pass in the forward evaluation and applies the
+ * incoming gradient in the backward evaluation with this call.
+ * GCP_ERR_ARG for a NULL pointer or n < 0. */
+gcp_status gcp_scale_async(gcp_ctx *ctx, const float *dscale, const float *x, float *y, int64_t n);
+
 /* One Adam step (Algorithm 1, one kernel over the flat parameter vector,
  * Sec. 3.1.3) with the gradient held by the context, t >= 1. */
 gcp_status gcp_adam_step(gcp_ctx *ctx, const gcp_adam_params *prm, int64_t t);

@@ -86,6 +86,7 @@ SIGNATURES = {
     "gcp_loss_async": (_i32, [_vp, _u64, _i64, _i64, _vp]),
     "gcp_grad": (_i32, [_vp, _u64, _i64, _i64, _vp, _vp]),
     "gcp_grad_async": (_i32, [_vp, _u64, _i64, _i64, _vp, _vp, _vp]),
+    "gcp_scale_async": (_i32, [_vp, _vp, _vp, _vp, _i64]),
     "gcp_adam_step": (_i32, [_vp, ctypes.POINTER(gcp_adam_params), _i64]),
     "gcp_step": (_i32, [_vp, _u64, _i64, _i64, ctypes.POINTER(gcp_adam_params), _i64, _vp]),
     "gcp_sync": (_i32, [_vp]),
@@ -275,6 +276,12 @@ class GcpContext:
     def grad_async(self, iter, p, q, dscale=None, G_out=None, dloss=None):
         _check(load().gcp_grad_async(self.handle, iter, p, q, _ptr(dscale), _ptr(G_out), _ptr(dloss)),
                self.handle)
+
+    def scale_async(self, dscale, x, y):
+        """y = dscale[0] * x on the context's stream (device tensors)."""
+        if x.numel() != y.numel():
+            raise ValueError("x and y differ in length")
+        _check(load().gcp_scale_async(self.handle, _ptr(dscale), _ptr(x), _ptr(y), x.numel()), self.handle)
 
     def loss_async(self, iter, p, q, dloss):
         _check(load().gcp_loss_async(self.handle, iter, p, q, _ptr(dloss)), self.handle)

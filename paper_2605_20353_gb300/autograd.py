@@ -2,11 +2,13 @@
 
 Forward: the sampled loss F~ = sum_s w_s f(x_s, m_s) of one sample set
 (Sec. 3.1.1 weights, Eq. gcp-model), reduced in FP64 by the fused kernel.
-Backward: the same fused kernel in gradient mode -- it redraws the samples
-from their counters and recomputes the Khatri-Rao row products, so nothing
-per sample is stored between the passes -- scaled on the device by the
-incoming gradient (Eq. gcp-gradient).  All arithmetic runs in libgcp.so;
-this module only moves pointers.
+When a factor needs a gradient, the same fused pass also forms the sampled
+gradient (Eq. gcp-gradient) with a unit seed, so each sample is drawn and
+its Khatri-Rao rows gathered once; nothing per sample is stored, only the
+gradient itself (sum_k I_k R floats).  Backward multiplies that gradient by
+the incoming one on the device.  Without factor gradients the forward pass
+computes the loss alone.  All arithmetic runs in libgcp.so; this module
+only moves pointers.
 """
 from __future__ import annotations
 
@@ -41,28 +43,30 @@ class GcpSampledLoss(torch.autograd.Function):
     @staticmethod
     def forward(fctx, ctx: GcpContext, iteration: int, p: int, q: int, *factors):
         staged = _stage_factors(ctx, factors)
-        loss = torch.empty(1, dtype=torch.float64, device=factors[0].device)
-        ctx.loss_async(iteration, p, q, loss)
+        dev = factors[0].device
+        loss = torch.empty(1, dtype=torch.float64, device=dev)
         fctx.gcp = ctx
-        fctx.args = (iteration, p, q)
-        fctx.staged = staged
-        fctx.save_for_backward(*factors)
+        fctx.G = None
+        if any(fctx.needs_input_grad[4:]):
+            fctx.G = torch.empty(ctx.num_params, dtype=torch.float32, device=dev)
+            ctx.grad_async(iteration, p, q, G_out=fctx.G, dloss=loss)
+        else:
+            ctx.loss_async(iteration, p, q, loss)
+        fctx.staged = staged  # alive until the stream has consumed them
         return loss.reshape(())
 
     @staticmethod
     def backward(fctx, grad_out):
         ctx: GcpContext = fctx.gcp
-        iteration, p, q = fctx.args
-        factors = fctx.saved_tensors
-        staged = _stage_factors(ctx, factors)  # the context may have served other calls since
         scale = grad_out.detach().to(torch.float32).reshape(1).contiguous()
-        G = torch.empty(ctx.num_params, dtype=torch.float32, device=factors[0].device)
-        ctx.grad_async(iteration, p, q, dscale=scale, G_out=G)
+        G = torch.empty_like(fctx.G)
+        ctx.scale_async(scale, fctx.G, G)
         grads, o = [], 0
-        for I in ctx.dims:
-            grads.append(G[o:o + I * ctx.rank].view(I, ctx.rank))
+        for k, I in enumerate(ctx.dims):
+            g = G[o:o + I * ctx.rank].view(I, ctx.rank)
+            grads.append(g if fctx.needs_input_grad[4 + k] else None)
             o += I * ctx.rank
-        fctx.staged = staged + [scale]  # alive until the stream has consumed them
+        fctx.staged = fctx.staged + [scale, fctx.G]  # alive until the stream has consumed them
         return (None, None, None, None, *grads)
 
 

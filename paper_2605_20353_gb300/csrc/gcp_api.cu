@@ -389,6 +389,13 @@ gcp_status do_step(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, const gcp_ad
     return GCP_OK;
 }
 
+// y = s[0] * x elementwise (x and y may be the same array).
+__global__ void k_scale(const float *s, const float *x, float *y, int64_t n) {
+    const float a = __ldg(s);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = a * x[i];
+}
+
 gcp_status copy_grad_out(gcp_ctx *c, float *G_out) {
     if (!G_out) return GCP_OK;
     GCP_CUDA(c, cudaMemcpy2DAsync(G_out, (size_t)c->R * 4, c->G, (size_t)c->Rp * 4, (size_t)c->R * 4,
@@ -693,6 +700,17 @@ gcp_status gcp_grad_async(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, const
     if (s) return s;
     if (dloss_out)
         GCP_CUDA(c, cudaMemcpyAsync(dloss_out, c->dloss, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    return GCP_OK;
+}
+
+gcp_status gcp_scale_async(gcp_ctx *c, const float *dscale, const float *x, float *y, int64_t n) {
+    if (!c) return fail(c, GCP_ERR_ARG, "NULL context");
+    if (!dscale || !x || !y || n < 0) return fail(c, GCP_ERR_ARG, "NULL array or negative length");
+    if (n == 0) return GCP_OK;
+    DeviceGuard g(c->device);
+    const int64_t want = (n + 255) / 256;
+    k_scale<<<(unsigned)(want < 8192 ? want : 8192), 256, 0, c->st>>>(dscale, x, y, n);
+    GCP_CUDA(c, cudaGetLastError());
     return GCP_OK;
 }
 

@@ -1,6 +1,7 @@
 """The autograd function of the sampled GCP loss against the FP64 oracle:
-forward = sampled loss, backward = the fused MTTKRP adjoint (samples redrawn,
-Khatri-Rao rows recomputed), scaled by the incoming gradient."""
+forward = sampled loss and, when a factor needs a gradient, the fused MTTKRP
+adjoint from the same pass; backward = that gradient scaled on the device
+by the incoming gradient."""
 import numpy as np
 import pytest
 
@@ -74,4 +75,27 @@ def test_autograd_dense_simulation_full_size(env):
     s = 1 << 22
     samples = oracle.uniform_samples(3003, 7, s, dims, X)
     check(env, ctx, fac, 7, s, 0, "gaussian", samples)
+    ctx.close()
+
+
+def test_autograd_loss_only_and_partial_grads(env):
+    """Without factor gradients the forward computes the loss alone, with
+    the same value; with only some factors requiring gradients, the others
+    get none and the rest match the oracle."""
+    gcp, torch, ag = env
+    dims = [30, 20, 10]
+    coords, vals = synth.uniform_sparse(dims, 900, 51, lam=2.0)
+    fac = synth.factors_uniform(dims, 8, 52, lo=0.1, hi=1.0)
+    ctx = gcp.gcp_create(dims, coords, vals, 8, "poisson", seed=53)
+    with torch.no_grad():
+        L0 = ag.sampled_loss(ctx, 3, 700, 800, [torch.tensor(a, device="cuda") for a in fac])
+    A = [torch.tensor(a, device="cuda", requires_grad=(k != 1)) for k, a in enumerate(fac)]
+    L1 = ag.sampled_loss(ctx, 3, 700, 800, A)
+    assert L0.item() == L1.item()  # the loss reduction is fixed-order in both passes
+    (2.5 * L1).backward()
+    idx, x, w, _ = oracle.stratified_samples(53, 3, 700, 800, dims, coords, vals)
+    _, Go = oracle.sampled_loss_grad(dims, fac, "poisson", idx, x, w)
+    assert A[1].grad is None
+    for k in (0, 2):
+        assert rel_err(A[k].grad.cpu().numpy(), 2.5 * Go[k]) <= TOL, k
     ctx.close()
