@@ -47,9 +47,8 @@ __global__ void k_radix_hist(const int32_t *__restrict__ keys, int key_stride, i
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive prefix sum of n ints in place, in three phases: each block of
-// kScanBlock elements scans itself and records its total; one block scans
-// the totals (and writes the grand total); each block adds its offset.
+// Scan phases: each block of kScanBlock elements scans itself in place and
+// records its total; one block scans the totals (and writes the grand total).
 __global__ void k_scan_blocks(int32_t *a, int64_t n, int32_t *block_sums) {
     __shared__ int32_t warp_tot[kT / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * (kScanBlock / kT);
@@ -109,28 +108,27 @@ __global__ void k_scan_top(int32_t *a, int64_t n, int32_t *total) {
     }
 }
 
-__global__ void k_scan_add(int32_t *a, int64_t n, const int32_t *block_sums) {
-    const int32_t off = block_sums[blockIdx.x];
-    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
-    for (int j = threadIdx.x; j < kScanBlock && base + j < n; j += kT) a[base + j] += off;
-}
-
-void scan_exclusive(int32_t *a, int64_t n, int32_t *total, int32_t *block_sums, cudaStream_t st) {
+// Exclusive prefix sum of n ints, left in two parts: a[i] holds the scan
+// within its block of kScanBlock elements and block_sums[i / kScanBlock]
+// the scan of the block totals, so the full value is their sum (consumers
+// add the two).  *total (if not NULL) receives the grand total.
+void scan_two_part(int32_t *a, int64_t n, int32_t *total, int32_t *block_sums, cudaStream_t st) {
     const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
     k_scan_blocks<<<(unsigned)nb, kT, 0, st>>>(a, n, block_sums);
     k_scan_top<<<1, kT, 0, st>>>(block_sums, nb, total);
-    k_scan_add<<<(unsigned)nb, kT, 0, st>>>(a, n, block_sums);
 }
 
 // Stable scatter of one 8-bit digit pass.  Keys of a tile are ranked in
 // index order: rounds of kT keys, warps in order, lanes in order.
 __global__ void k_radix_scatter(const int32_t *__restrict__ keys, int key_stride, const int32_t *__restrict__ vals,
-                                int64_t n, int shift, const int32_t *__restrict__ offsets, int ntiles,
+                                int64_t n, int shift, const int32_t *__restrict__ offsets,
+                                const int32_t *__restrict__ offset_blocks, int ntiles,
                                 int32_t *__restrict__ keys_out, int32_t *__restrict__ vals_out) {
     __shared__ int running[256];
     __shared__ int wcount[kT / 32][256];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    running[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    const int64_t oi = (int64_t)threadIdx.x * ntiles + blockIdx.x;  // thread = digit
+    running[threadIdx.x] = offsets[oi] + offset_blocks[oi / kScanBlock];
     for (int w = 0; w < kT / 32; ++w) wcount[w][threadIdx.x] = 0;
     __syncthreads();
     const int64_t first = (int64_t)blockIdx.x * kTile;
@@ -371,8 +369,8 @@ __global__ void k_carry_flags(const int32_t *ckey, int64_t n, int32_t *flag) {
 
 // Order-preserving compaction of the used carry slots, one 16-byte quad of
 // a vector per thread (Rp = 4 << log2q).
-__global__ void k_carry_compact(const int32_t *ckey, const float *cvec, int64_t n, const int32_t *pos, int log2q,
-                                int32_t *okey, float *ovec) {
+__global__ void k_carry_compact(const int32_t *ckey, const float *cvec, int64_t n, const int32_t *pos,
+                                const int32_t *pos_blocks, int log2q, int32_t *okey, float *ovec) {
     const int Rp = 4 << log2q;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (n << log2q);
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -380,7 +378,7 @@ __global__ void k_carry_compact(const int32_t *ckey, const float *cvec, int64_t 
         const int c = 4 * (int)(e & ((1 << log2q) - 1));
         const int32_t key = ckey[i];
         if (key < 0) continue;
-        const int64_t o = pos[i];
+        const int64_t o = pos[i] + pos_blocks[i / kScanBlock];
         *reinterpret_cast<float4 *>(ovec + o * Rp + c) = *reinterpret_cast<const float4 *>(cvec + i * Rp + c);
         if (c == 0) okey[o] = key;
     }
@@ -524,8 +522,9 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
         int32_t *kout = kA, *vout = vA;
         for (int shift = 0; shift < bits; shift += 8) {
             k_radix_hist<<<(int)ntiles, kT, 0, st>>>(kin, kstride, S, shift, hist, (int)ntiles);
-            scan_exclusive(hist, 256 * ntiles, nullptr, bsum, st);
-            k_radix_scatter<<<(int)ntiles, kT, 0, st>>>(kin, kstride, vin, S, shift, hist, (int)ntiles, kout, vout);
+            scan_two_part(hist, 256 * ntiles, nullptr, bsum, st);
+            k_radix_scatter<<<(int)ntiles, kT, 0, st>>>(kin, kstride, vin, S, shift, hist, bsum, (int)ntiles, kout,
+                                                        vout);
             DET_CUDA(cudaGetLastError());
             kin = kout;
             vin = vout;
@@ -548,9 +547,9 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
         int64_t nslots = 2 * nch;
         while (nch > 1) {
             k_carry_flags<<<grid_for(nslots, kT), kT, 0, st>>>(ckey_out, nslots, cpos);
-            scan_exclusive(cpos, nslots, dlen, bsum, st);
+            scan_two_part(cpos, nslots, dlen, bsum, st);
             k_carry_compact<<<grid_for(nslots * (c->Rp / 4), kT), kT, 0, st>>>(ckey_out, cvec_out, nslots, cpos,
-                                                                               log2q, lkey, lvec);
+                                                                               bsum, log2q, lkey, lvec);
             nch = (nslots + kChunk - 1) / kChunk;
             nslots = 2 * nch;
             std::swap(ckey_in, ckey_out);
