@@ -277,10 +277,13 @@ __global__ void __launch_bounds__(kThreads) k_batch_fused(const int4 *__restrict
 
 // ------------------------------------------------- per-client small kernels
 // grid.y = client; blocks of grid.x stride over that client's elements.
+// G = 0, one 16-byte quad per thread and step (nparam is a multiple of 4).
 __global__ void k_batch_zero(const ClientAux *__restrict__ aux) {
     const ClientAux &a = aux[blockIdx.y];
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.nparam; e += (int64_t)gridDim.x * blockDim.x)
-        a.G[e] = 0.0f;
+    float4 *G = reinterpret_cast<float4 *>(a.G);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (a.nparam >> 2);
+         e += (int64_t)gridDim.x * blockDim.x)
+        G[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
 // G(hot row) += sum of the replicas (all loads first), replicas cleared.
@@ -296,7 +299,8 @@ __global__ void k_batch_fold(const ClientAux *__restrict__ aux) {
         for (int r = 0; r < gcpk::kReplicas; ++r) t += v[r];
 #pragma unroll
         for (int r = 0; r < gcpk::kReplicas; ++r) a.Grep[r * n + e] = 0.0f;
-        a.G[(int64_t)a.hot_row[e / a.Rp] * a.Rp + e % a.Rp] += t;
+        const int log2Rp = __ffs(a.Rp) - 1;  // Rp is a power of two
+        a.G[((int64_t)a.hot_row[e >> log2Rp] << log2Rp) + (e & (a.Rp - 1))] += t;
     }
 }
 
@@ -341,17 +345,35 @@ __global__ void k_batch_adam(const ClientAux *__restrict__ aux, const double *__
         c[6] = (float)adam[4];
     }
     __syncthreads();
-    __nv_bfloat16 *Abf = static_cast<__nv_bfloat16 *>(a.Abf);
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.nparam; e += (int64_t)gridDim.x * blockDim.x) {
-        if ((int)(e % a.Rp) >= a.R) continue;
-        const float g = a.G[e];
-        const float b = c[1] * a.B[e] + (1.0f - c[1]) * g;
-        const float cc = c[2] * a.C[e] + (1.0f - c[2]) * g * g;
-        a.B[e] = b;
-        a.C[e] = cc;
-        const float x = fmaxf(a.A[e] - c[0] * ((b * c[3]) / sqrtf(cc * c[4] + c[5])), c[6]);
-        a.A[e] = x;
-        if (Abf) Abf[e] = __float2bfloat16_rn(x);
+    // one 16-byte quad of A, B, C and G per thread and step: nparam and Rp
+    // are multiples of 4 and Rp is a power of two, so a quad lies in one row
+    uint2 *Abf = static_cast<uint2 *>(a.Abf);
+    const int cmask = a.Rp - 1;
+    for (int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; qi < (a.nparam >> 2);
+         qi += (int64_t)gridDim.x * blockDim.x) {
+        const int col = (int)((qi << 2) & cmask);
+        if (col >= a.R) continue;  // a padded quad stays zero
+        const float4 g4 = reinterpret_cast<const float4 *>(a.G)[qi];
+        float4 b4 = reinterpret_cast<const float4 *>(a.B)[qi];
+        float4 c4 = reinterpret_cast<const float4 *>(a.C)[qi];
+        float4 x4 = reinterpret_cast<const float4 *>(a.A)[qi];
+        const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+        float bv[4] = {b4.x, b4.y, b4.z, b4.w}, cv[4] = {c4.x, c4.y, c4.z, c4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (col + j >= a.R) continue;  // padded columns stay zero
+            const float g = gv[j];
+            bv[j] = c[1] * bv[j] + (1.0f - c[1]) * g;
+            cv[j] = c[2] * cv[j] + (1.0f - c[2]) * g * g;
+            xv[j] = fmaxf(xv[j] - c[0] * ((bv[j] * c[3]) / sqrtf(cv[j] * c[4] + c[5])), c[6]);
+        }
+        reinterpret_cast<float4 *>(a.B)[qi] = make_float4(bv[0], bv[1], bv[2], bv[3]);
+        reinterpret_cast<float4 *>(a.C)[qi] = make_float4(cv[0], cv[1], cv[2], cv[3]);
+        reinterpret_cast<float4 *>(a.A)[qi] = make_float4(xv[0], xv[1], xv[2], xv[3]);
+        if (Abf) {
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(xv[0], xv[1]), hi = __floats2bfloat162_rn(xv[2], xv[3]);
+            Abf[qi] = make_uint2(*reinterpret_cast<const unsigned *>(&lo), *reinterpret_cast<const unsigned *>(&hi));
+        }
     }
 }
 

@@ -372,7 +372,8 @@ __device__ __forceinline__ void fold_range(float *__restrict__ G, float *__restr
         for (int r = 0; r < kReplicas; ++r) t += v[r];
 #pragma unroll
         for (int r = 0; r < kReplicas; ++r) Grep[r * plane + e] = 0.0f;
-        const int slot = (int)(e / Rp), col = (int)(e % Rp);
+        const int log2Rp = __ffs(Rp) - 1;  // Rp is a power of two
+        const int slot = (int)(e >> log2Rp), col = (int)(e & (Rp - 1));
         G[(int64_t)hot_row[slot] * Rp + col] += t;
     }
 }
@@ -448,20 +449,47 @@ __global__ void k_build_records(const int32_t *__restrict__ coords, const float 
 // ------------------------------------------------------------------ Adam
 // Algorithm 1 on the flat parameter vector (Sec. 3.1.3); padded columns
 // (col >= R) stay zero.  With BF16 storage the kernel-read copy is refreshed.
+// Algorithm 1 on one 16-byte quad of parameters (columns col..col+3 of one
+// row); padded columns (>= R) stay as they are (zero).  Abf, if not NULL,
+// receives the BF16 copy of the quad.
+__device__ __forceinline__ void adam_quad(float4 &a4, float4 &b4, float4 &c4, const float4 g4, int col, int R,
+                                          float lr, float beta1, float beta2, float c1inv, float c2inv, float eps,
+                                          float lower, uint2 *Abf) {
+    float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w}, cv[4] = {c4.x, c4.y, c4.z, c4.w};
+    const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (col + j >= R) continue;
+        const float g = gv[j];
+        bv[j] = beta1 * bv[j] + (1.0f - beta1) * g;
+        cv[j] = beta2 * cv[j] + (1.0f - beta2) * g * g;
+        av[j] = fmaxf(av[j] - lr * ((bv[j] * c1inv) / sqrtf(cv[j] * c2inv + eps)), lower);
+    }
+    a4 = make_float4(av[0], av[1], av[2], av[3]);
+    b4 = make_float4(bv[0], bv[1], bv[2], bv[3]);
+    c4 = make_float4(cv[0], cv[1], cv[2], cv[3]);
+    if (Abf) {
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(av[0], av[1]), hi = __floats2bfloat162_rn(av[2], av[3]);
+        *Abf = make_uint2(*reinterpret_cast<const unsigned *>(&lo), *reinterpret_cast<const unsigned *>(&hi));
+    }
+}
+
+// Algorithm 1 over the flat parameter vector, one quad per thread and step
+// (n and Rp are multiples of 4, Rp a power of two, so a quad is in one row).
 __global__ void k_adam(int64_t n, int Rp, int R, float *__restrict__ A, float *__restrict__ B,
                        float *__restrict__ C, const float *__restrict__ G, float lr, float beta1, float beta2,
                        float c1inv, float c2inv, float eps, float lower, __nv_bfloat16 *Abf) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        if ((int)(e % Rp) >= R) continue;
-        const float g = G[e];
-        const float b = beta1 * B[e] + (1.0f - beta1) * g;
-        const float c = beta2 * C[e] + (1.0f - beta2) * g * g;
-        B[e] = b;
-        C[e] = c;
-        float a = A[e] - lr * ((b * c1inv) / sqrtf(c * c2inv + eps));
-        a = fmaxf(a, lower);
-        A[e] = a;
-        if (Abf) Abf[e] = __float2bfloat16_rn(a);
+    for (int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; qi < (n >> 2);
+         qi += (int64_t)gridDim.x * blockDim.x) {
+        const int col = (int)((qi << 2) & (Rp - 1));
+        if (col >= R) continue;
+        float4 a4 = reinterpret_cast<const float4 *>(A)[qi], b4 = reinterpret_cast<const float4 *>(B)[qi],
+               c4 = reinterpret_cast<const float4 *>(C)[qi];
+        adam_quad(a4, b4, c4, reinterpret_cast<const float4 *>(G)[qi], col, R, lr, beta1, beta2, c1inv, c2inv, eps,
+                  lower, Abf ? reinterpret_cast<uint2 *>(Abf) + qi : nullptr);
+        reinterpret_cast<float4 *>(A)[qi] = a4;
+        reinterpret_cast<float4 *>(B)[qi] = b4;
+        reinterpret_cast<float4 *>(C)[qi] = c4;
     }
 }
 
@@ -491,11 +519,12 @@ __global__ void __launch_bounds__(kThreads) k_post_step(PostSpec P) {
         }
     }
     const int64_t plane = (int64_t)P.Htot * P.Rp;
+    const int log2Rp = __ffs(P.Rp) - 1;  // Rp is a power of two
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < P.n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int row = (int)(e / P.Rp), col = (int)(e % P.Rp);
+        const int row = (int)(e >> log2Rp), col = (int)(e & (P.Rp - 1));
         float g = P.G[e];
         const int hs = P.hot_slot ? __ldg(P.hot_slot + row) : -1;
-        if (hs >= 0) {
+        if (hs >= 0) {  // all replica loads first, added in replica order, then cleared
             float v[kReplicas];
             const int64_t o = (int64_t)hs * P.Rp + col;
 #pragma unroll
