@@ -136,6 +136,23 @@ def _ptr(t):
     return t.data_ptr()
 
 
+def _check_buf(t, n, dtype, name):
+    """The C ABI cannot see buffer sizes: refuse a buffer that is too small,
+    of another element type, or not contiguous before its address is passed."""
+    if t is None:
+        return
+    if isinstance(t, np.ndarray):
+        ok_type = t.dtype == np.dtype(dtype)
+        size, contiguous = t.size, t.flags["C_CONTIGUOUS"]
+    else:
+        import torch
+
+        ok_type = t.dtype == {"float32": torch.float32, "float64": torch.float64}[dtype]
+        size, contiguous = t.numel(), t.is_contiguous()
+    if not ok_type or size < n or not contiguous:
+        raise ValueError(f"{name} must be a contiguous {dtype} buffer of at least {n} elements")
+
+
 def _stream_handle(stream):
     import torch
 
@@ -221,7 +238,8 @@ class GcpContext:
                     a = np.ascontiguousarray(a, dtype=np.float32)
                 else:
                     a = a.detach().to(torch.float32).contiguous()
-                assert tuple(a.shape) == (self.dims[k], self.rank)
+                if tuple(a.shape) != (self.dims[k], self.rank):
+                    raise ValueError(f"factor {k} has shape {tuple(a.shape)}, expected {(self.dims[k], self.rank)}")
                 _check(load().gcp_set_factor(self.handle, k, _ptr(a)), self.handle)
                 if not isinstance(a, np.ndarray):
                     self._keep = a
@@ -230,8 +248,7 @@ class GcpContext:
         a = factors
         if isinstance(a, np.ndarray):
             a = np.ascontiguousarray(a, dtype=np.float32)
-        n = a.size if isinstance(a, np.ndarray) else a.numel()
-        assert n == self.num_params
+        _check_buf(a, self.num_params, "float32", "factors")
         _check(load().gcp_set_factors(self.handle, _ptr(a)), self.handle)
         self.sync()
 
@@ -268,22 +285,28 @@ class GcpContext:
 
     def grad(self, iter, p, q, G_out=None, want_loss=True):
         """Sampled gradient; returns (loss or None, G_out)."""
+        _check_buf(G_out, self.num_params, "float32", "G_out")
         out = ctypes.c_double(0.0)
         _check(load().gcp_grad(self.handle, iter, p, q, _ptr(G_out), ctypes.byref(out) if want_loss else None),
                self.handle)
         return (out.value if want_loss else None), G_out
 
     def grad_async(self, iter, p, q, dscale=None, G_out=None, dloss=None):
+        _check_buf(dscale, 1, "float32", "dscale")
+        _check_buf(G_out, self.num_params, "float32", "G_out")
+        _check_buf(dloss, 1, "float64", "dloss")
         _check(load().gcp_grad_async(self.handle, iter, p, q, _ptr(dscale), _ptr(G_out), _ptr(dloss)),
                self.handle)
 
     def scale_async(self, dscale, x, y):
         """y = dscale[0] * x on the context's stream (device tensors)."""
-        if x.numel() != y.numel():
-            raise ValueError("x and y differ in length")
+        _check_buf(dscale, 1, "float32", "dscale")
+        _check_buf(x, 0, "float32", "x")
+        _check_buf(y, x.numel(), "float32", "y")
         _check(load().gcp_scale_async(self.handle, _ptr(dscale), _ptr(x), _ptr(y), x.numel()), self.handle)
 
     def loss_async(self, iter, p, q, dloss):
+        _check_buf(dloss, 1, "float64", "dloss")
         _check(load().gcp_loss_async(self.handle, iter, p, q, _ptr(dloss)), self.handle)
 
     def adam_step(self, prm: AdamParams, t: int):
@@ -292,6 +315,7 @@ class GcpContext:
 
     def step(self, iter, p, q, prm: AdamParams, t: int, dloss=None):
         """Sampled gradient + Adam step t in one call (G is cleared after)."""
+        _check_buf(dloss, 1, "float64", "dloss")
         c = prm.c()
         _check(load().gcp_step(self.handle, iter, p, q, ctypes.byref(c), t, _ptr(dloss)), self.handle)
 
@@ -418,7 +442,18 @@ def gcp_grad_samples_noalloc(dims, rank, loss, idx, x, w, A, G, loss_out, stream
     """Loss and gradient of a given sample list with no device allocation
     (for callers that cannot allocate).  idx/x/w/A/G/loss_out are device
     tensors; loss_out holds 2 doubles (loss, skipped samples).  Asynchronous."""
+    import torch
+
     d = np.ascontiguousarray(dims, dtype=np.int64)
+    S = int(idx.shape[0])
+    if idx.dtype != torch.int32 or tuple(idx.shape) != (S, len(d)) or not idx.is_contiguous():
+        raise ValueError(f"idx must be a contiguous int32 tensor of shape (nsamples, {len(d)})")
+    nparam = int(d.sum()) * int(rank)
+    _check_buf(x, S, "float32", "x")
+    _check_buf(w, S, "float32", "w")
+    _check_buf(A, nparam, "float32", "A")
+    _check_buf(G, nparam, "float32", "G")
+    _check_buf(loss_out, 2, "float64", "loss_out")
     _check(load().gcp_grad_samples_noalloc(len(d), d.ctypes.data, rank, LOSSES[loss], int(idx.shape[0]), _ptr(idx),
                                            _ptr(x), _ptr(w), _ptr(A), _ptr(G), _ptr(loss_out),
                                            _stream_handle(stream)), None)

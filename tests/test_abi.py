@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -103,3 +104,25 @@ def test_fit_presets_are_valid_adam_settings():
         assert 0 < p["decay"] < 1, name
     assert gcp.FIT_PRESETS["gcp_sgd_tuned"]["adam"].lr == 0.035817
     assert gcp.FIT_PRESETS["gcp_fedadam_tuned"]["meta_rate"] == 0.029976
+
+
+def test_binding_refuses_undersized_or_mistyped_buffers():
+    """The C ABI takes bare device pointers, so the binding checks element
+    type, length and contiguity before it passes an address."""
+    import torch
+
+    import paper_2605_20353_gb300 as gcp
+
+    gcp._check_buf(np.zeros(10, np.float32), 10, "float32", "G_out")
+    gcp._check_buf(torch.zeros(3, dtype=torch.float64), 1, "float64", "dloss")
+    gcp._check_buf(None, 10, "float32", "G_out")
+    bad = [
+        (np.zeros(9, np.float32), "float32"),                   # too short
+        (np.zeros(10, np.float64), "float32"),                  # wrong type
+        (np.zeros((10, 2), np.float32)[:, 0], "float32"),       # strided
+        (torch.zeros(10, dtype=torch.float32), "float64"),      # a float32 loss buffer
+        (torch.zeros(20, dtype=torch.float32)[::2], "float32"),  # strided tensor
+    ]
+    for buf, dtype in bad:
+        with pytest.raises(ValueError):
+            gcp._check_buf(buf, 10 if dtype == "float32" else 1, dtype, "buf")
