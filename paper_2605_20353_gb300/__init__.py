@@ -391,8 +391,10 @@ class GcpBatch:
         lib = load()
         self.clients = list(clients)  # keep the contexts alive
         arr = (ctypes.c_void_p * len(self.clients))(*[c.handle for c in self.clients])
-        pp = np.ascontiguousarray(p, dtype=np.int64)
-        qq = np.ascontiguousarray(q, dtype=np.int64)
+        pp = np.ascontiguousarray(p, dtype=np.int64).reshape(-1)
+        qq = np.ascontiguousarray(q, dtype=np.int64).reshape(-1)
+        if len(pp) != len(self.clients) or len(qq) != len(self.clients):
+            raise ValueError("p and q need one entry per client")
         h = ctypes.c_void_p()
         rc = lib.gcp_batch_create(len(self.clients), ctypes.cast(arr, ctypes.c_void_p), pp.ctypes.data,
                                   qq.ctypes.data, ctypes.byref(h))

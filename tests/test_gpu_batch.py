@@ -141,6 +141,8 @@ def test_batch_rejects_mismatched_clients(env, shards):
         gcp.GcpBatch([a, c], [10, 10], [10, 10])
     with pytest.raises(gcp.GcpError):
         gcp.GcpBatch([a], [-1], [10])
+    with pytest.raises(ValueError):
+        gcp.GcpBatch([a], [10, 10], [10])  # one count per client
 
 
 def test_batch_of_64_clients_full_size_against_oracle(env):
