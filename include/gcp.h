@@ -157,7 +157,10 @@ gcp_status gcp_create(int32_t ndim, const int64_t *dims, int64_t nnz, const int3
 /* Create a context for a dense tensor X (host or device, prod(dims) floats,
  * row-major, last mode fastest).  Sampling is uniform over all cells with
  * weight M/p (the stochastic gradient of Sec. 3.1.1 with Y sampled
- * uniformly); q must be 0 in the sampling calls.  X is copied. */
+ * uniformly); q must be 0 in the sampling calls.  X is copied, and its
+ * values are checked on the device as gcp_create checks nonzeros:
+ * GCP_ERR_ARG for a non-finite value, GCP_ERR_DOMAIN for a value outside
+ * the loss's domain; also GCP_ERR_OOM, GCP_ERR_CUDA.  On error *out is NULL. */
 gcp_status gcp_create_dense(int32_t ndim, const int64_t *dims, const float *X, int32_t rank,
                             int32_t loss, const gcp_options *opt, gcp_ctx **out);
 

@@ -376,6 +376,7 @@ def gcp_create_dense(dims, X, rank, loss, dtype="fp32", seed=0, stream=None, lan
     d = np.ascontiguousarray(dims, dtype=np.int64)
     if isinstance(X, np.ndarray):
         X = np.ascontiguousarray(X, dtype=np.float32)
+    _check_buf(X, int(np.prod(d, dtype=np.float64)), "float32", "X")
     opt = _options(dtype, "atomic", "uniform", seed, stream, 64, 0.3, lane_cols)
     h = ctypes.c_void_p()
     _check(lib.gcp_create_dense(len(d), d.ctypes.data, _ptr(X), rank, LOSSES[loss], ctypes.byref(opt),

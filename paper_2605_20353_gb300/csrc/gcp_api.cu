@@ -67,6 +67,8 @@ const char *status_text(gcp_status s) {
     case GCP_ERR_HASH_FULL: return "nonzero hash set is full";
     case GCP_ERR_SAMPLER_EXHAUSTED: return "a zero draw hit nonzeros max_attempts times (tensor too dense)";
     case GCP_ERR_NONFINITE: return "non-finite loss";
+    case GCP_ERR_ARG: return "non-finite value in the dense tensor";
+    case GCP_ERR_DOMAIN: return "value outside the loss's domain";
     default: return "device error";
     }
 }
@@ -389,6 +391,22 @@ gcp_status do_step(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, const gcp_ad
     return GCP_OK;
 }
 
+// Values of a dense tensor: bit GCP_ERR_ARG for a non-finite value, bit
+// GCP_ERR_DOMAIN for one outside the loss's domain (the host checks of a
+// sparse tensor's values, on the device).
+__global__ void k_check_dense(const float *X, int64_t n, int loss, int *status) {
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = X[i];
+        if (!isfinite(x))
+            bad |= 1 << GCP_ERR_ARG;
+        else if ((loss == GCP_POISSON && x < 0.0f) || (loss == GCP_GAMMA && x <= 0.0f) ||
+                 (loss == GCP_BERNOULLI_LOGIT && x != 1.0f && x != 0.0f))
+            bad |= 1 << GCP_ERR_DOMAIN;
+    }
+    if (bad) atomicOr(status, bad);
+}
+
 // y = s[0] * x elementwise (x and y may be the same array).
 __global__ void k_scale(const float *s, const float *x, float *y, int64_t n) {
     const float a = __ldg(s);
@@ -592,10 +610,23 @@ gcp_status gcp_create_dense(int32_t ndim, const int64_t *dims, const float *X, i
     const size_t bytes = (size_t)c->M * 4;
     cudaError_t e;
     if ((e = cudaMalloc(&c->X, bytes)) ||
-        (e = cudaMemcpyAsync(c->X, X, bytes, cudaMemcpyDefault, c->st)) || (e = cudaStreamSynchronize(c->st))) {
+        (e = cudaMemcpyAsync(c->X, X, bytes, cudaMemcpyDefault, c->st))) {
         destroy_buffers(c);
         delete c;
         return cuda_fail(nullptr, e, "copying the dense tensor");
+    }
+    k_check_dense<<<4096, 256, 0, c->st>>>(c->X, (int64_t)c->M, c->loss, c->status);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        destroy_buffers(c);
+        delete c;
+        return cuda_fail(nullptr, e, "checking the dense tensor");
+    }
+    s = collect(c);  // synchronises
+    if (s) {
+        g_create_err = c->err;
+        destroy_buffers(c);
+        delete c;
+        return s;
     }
     *out = c;
     return GCP_OK;

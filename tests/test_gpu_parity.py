@@ -340,6 +340,20 @@ def test_largest_sample_count_per_call(env):
     ctx.close()
 
 
+@pytest.mark.parametrize("loss,bad,status", [("gaussian", np.nan, "ERR_ARG"), ("gaussian", np.inf, "ERR_ARG"),
+                                              ("poisson", -1.0, "ERR_DOMAIN"), ("bernoulli", 0.5, "ERR_DOMAIN")])
+def test_dense_values_checked_at_creation(env, loss, bad, status):
+    gcp, torch = env
+    dims = [6, 5, 4]
+    X = np.ones(int(np.prod(dims)), np.float32)
+    X[77] = bad
+    with pytest.raises(gcp.GcpError) as e:
+        gcp.gcp_create_dense(dims, X, 4, loss)
+    assert e.value.status == status
+    X[77] = 0.0
+    gcp.gcp_create_dense(dims, X, 4, loss).close()  # a valid tensor still builds
+
+
 def test_duplicate_nonzeros_rejected(env):
     gcp, torch = env
     coords = np.array([[0, 1, 1], [2, 0, 1], [0, 1, 1]], dtype=np.int32)
