@@ -149,6 +149,67 @@ def cpu_oracle_rate(w, skeys, n_samples, seed=3002, t=5):
     return n_samples / (time.perf_counter() - t0)
 
 
+_POOL_W = None
+
+
+def _pool_init(paths):
+    """Spawned oracle worker: map the workload's arrays read-only (shared
+    page cache, no per-worker copy)."""
+    global _POOL_W
+    import numpy as np
+
+    _POOL_W = {k: np.load(v, mmap_mode="r") for k, v in paths.items()}
+
+
+def _pool_task(task):
+    """One worker's share: the oracle as it stands on n samples of iteration t."""
+    import oracle
+
+    seed, t, n, dims, factors, loss = task
+    W = _POOL_W
+    p = n // 2
+    t0 = time.perf_counter()
+    idx, x, wt, _ = oracle.stratified_samples(seed, t, p, n - p, dims, W["coords"], W["vals"], skeys=W["skeys"])
+    oracle.sampled_loss_grad(dims, factors, loss, idx, x, wt)
+    return n, time.perf_counter() - t0
+
+
+class OraclePool:
+    """The unmodified oracle on all host cores: `workers` spawned processes
+    that map the workload's arrays read-only; run() gives each worker its own
+    iteration's samples and returns (samples, wall seconds of the slowest)."""
+
+    def __init__(self, w, skeys, workers, name="zipf_count_full"):
+        import multiprocessing as mp
+
+        import numpy as np
+
+        self.w, self.workers = w, workers
+        d = os.path.join(os.environ.get("GCP_CACHE_DIR") or os.path.join(ROOT, "_cache"), f"pool_{name}")
+        os.makedirs(d, exist_ok=True)
+        paths = {}
+        for k, a in (("coords", w["coords"]), ("vals", w["vals"]), ("skeys", skeys)):
+            paths[k] = os.path.join(d, k + ".npy")
+            if not os.path.exists(paths[k]):
+                tmp = paths[k] + f".tmp{os.getpid()}.npy"
+                np.save(tmp, np.ascontiguousarray(a))
+                os.replace(tmp, paths[k])
+        ctx = mp.get_context("spawn")  # never fork a process that holds a CUDA context
+        self.pool = ctx.Pool(workers, initializer=_pool_init, initargs=(paths,))
+        self.run(256, 10_000)  # start-up and first page faults, untimed
+
+    def run(self, n_per_worker, t0, seed=3002):
+        w = self.w
+        tasks = [(seed, t0 + i, n_per_worker, w["dims"], w["factors"], w["loss"]) for i in range(self.workers)]
+        start = time.perf_counter()
+        out = self.pool.map(_pool_task, tasks, chunksize=1)
+        return sum(n for n, _ in out), time.perf_counter() - start
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def cpu_baseline(w, target_s=10.0):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample."""
     import numpy as np
@@ -159,9 +220,28 @@ def cpu_baseline(w, target_s=10.0):
     probe = cpu_oracle_rate(w, skeys, 1 << 14)
     n = int(min(w["p"] + w["q"], max(1 << 14, probe * target_s)))
     rate = cpu_oracle_rate(w, skeys, n)
-    return {"value": rate, "unit": "samples/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} samples ({n // 2} nonzero + {n - n // 2} zero) of the same workload, "
-                      f"sampling + FP64 loss + all-mode gradient, one thread"}
+    single = {"value": rate, "unit": "samples/s", "cores": 1, "kind": "oracle",
+              "sample": f"{n} samples ({n // 2} nonzero + {n - n // 2} zero) of the same workload, "
+                        f"sampling + FP64 loss + all-mode gradient, one thread"}
+    cores = os.cpu_count() or 1
+    if cores < 2:
+        return single
+    try:
+        n_core = max(1 << 12, int(probe * target_s))
+        pool = OraclePool(w, skeys, cores)
+        try:
+            done, wall = pool.run(n_core, 1000)
+        finally:
+            pool.close()
+        all_rate = done / wall
+    except Exception as e:  # report the one-thread figure rather than none
+        single["all_cores_error"] = repr(e)[:200]
+        return single
+    return {"value": all_rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} spawned processes, each {n_core} samples ({n_core // 2} nonzero + "
+                      f"{n_core - n_core // 2} zero) of its own iteration of the same workload; sampling + FP64 "
+                      f"loss + all-mode gradient; total samples / wall time",
+            "single_thread": single}
 
 
 def run_reference(args):
@@ -175,26 +255,51 @@ def run_reference(args):
     w = workload()
     skeys = oracle.sorted_keys(w["dims"], w["coords"])
     probe = cpu_oracle_rate(w, skeys, 1 << 12)
-    per_step = max(64, int(probe * 90.0 / max(1, args.steps + args.warmup)))
-    per_step = min(per_step, w["p"] + w["q"])
-    for i in range(args.warmup):
-        cpu_oracle_rate(w, skeys, per_step, t=100 + i)
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        cpu_oracle_rate(w, skeys, per_step, t=i)
-    dt = time.perf_counter() - t0
-    value = per_step * args.steps / dt
+    cores = os.cpu_count() or 1
+    # each step: every core runs the oracle on its share of a bounded sample,
+    # sized so warm-up + timed steps take about 90 s in all
+    per_core = max(64, int(probe * 90.0 / max(1, args.steps + args.warmup)))
+    per_core = min(per_core, (w["p"] + w["q"]) // cores)
+    pool = OraclePool(w, skeys, cores)
+    try:
+        for i in range(args.warmup):
+            pool.run(per_core, 100 + 64 * i)
+        done, dt = 0, 0.0
+        for i in range(args.steps):
+            n, s = pool.run(per_core, 1_000_000 + 64 * i)
+            done += n
+            dt += s
+    finally:
+        pool.close()
+    per_step = done // args.steps
+    value = done / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "samples_per_step": per_step},
-            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} samples per step of the same workload"},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} samples per step of the same workload ({per_core} per core, "
+                                       f"{cores} spawned processes, each on its own iteration)"},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def batched_variant(gcp, torch, stream, steps=20):
+def oracle_rate(run, n0=1 << 12, target_s=4.0, cap=None):
+    """Single-thread oracle samples/s: run(n) draws and differentiates n
+    samples; a probe of n0 sizes one bounded run of about target_s seconds."""
+    t = time.perf_counter()
+    k = run(n0) or n0
+    r = k / (time.perf_counter() - t)
+    n = max(n0, int(r * target_s))
+    if cap:
+        n = min(n, cap)
+    t = time.perf_counter()
+    k = run(n) or n
+    return {"value": k / (time.perf_counter() - t), "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} samples, one thread"}
+
+
+def batched_variant(gcp, torch, stream, steps=20, with_oracle=True):
     """64 independent 3-way client shards (federated clients simulated on one
     GPU): mode sizes U{200..5000}, nnz log-uniform in [1e4, 2e6], values
     1+Poisson(2), Poisson loss, rank 16, BF16 factors, p_c = q_c =
@@ -219,6 +324,23 @@ def batched_variant(gcp, torch, stream, steps=20):
 
     res = {"workload": "64 clients, dims U{200..5000}^3, nnz log-uniform [1e4, 2e6], Poisson, rank 16",
            "samples_per_local_step": samples_per_step, "tau": tau}
+    if with_oracle:
+        import oracle
+
+        skeys = [oracle.sorted_keys(dims, coords) for dims, coords, _ in shards]
+        facs = [synth.factors_uniform(dims, 16, 6000 + i, lo=0.1, hi=1.0) for i, (dims, _, _) in enumerate(shards)]
+
+        def run(n):  # about n samples over the clients in proportion to their p_c + q_c
+            done = 0
+            for i, (dims, coords, vals) in enumerate(shards):
+                m = max(2, int(n * P[i] / sum(P)))
+                idx, x, wt, _ = oracle.stratified_samples(5000 + i, 3, m // 2, m - m // 2, dims, coords, vals,
+                                                          skeys=skeys[i])
+                oracle.sampled_loss_grad(dims, facs[i], "poisson", idx, x, wt)
+                done += m
+            return done
+
+        res["cpu_oracle"] = oracle_rate(run, n0=1 << 14)
     clients = make("bf16")
     batch = gcp.GcpBatch(clients, P, P)
     best, times = autotune.tune_batch(batch, adam, tau=tau, reps=2)
@@ -260,7 +382,7 @@ def batched_variant(gcp, torch, stream, steps=20):
     return res
 
 
-def hbm_resident_variant(gcp, torch, stream, launches=20):
+def hbm_resident_variant(gcp, torch, stream, launches=20, dtypes=("fp32", "bf16")):
     """Factors too large for L2: mode sizes near the paper's Amazon tensor
     (4.8M x 1.7M x 1.1M; its third mode is shortened from 1.8M so the cell
     count stays below 2^63), 2e7 uniform nonzeros with values 1+Poisson(2),
@@ -280,7 +402,7 @@ def hbm_resident_variant(gcp, torch, stream, launches=20):
     fac = synth.factors_uniform(dims, 16, 2006, lo=0.1, hi=1.0)
     S = 1 << 20
     res = {"workload": "4.8Mx1.7Mx1.1M, 2e7 uniform nnz, rank 16, Poisson, p=q=2^20 (factors 486 MB FP32)"}
-    for dtype in ("fp32", "bf16"):
+    for dtype in dtypes:
         ctx = gcp.gcp_create(dims, w["coords"], w["vals"], 16, "poisson", dtype=dtype, seed=9, stream=stream)
         ctx.set_factors(fac)
         for i in range(3):
@@ -298,7 +420,8 @@ def hbm_resident_variant(gcp, torch, stream, launches=20):
                                            4 if dtype == "fp32" else 2)
         res[dtype] = {"kernel_ms_per_launch": per, "samples_per_s": 2 * S / (per / 1e3),
                       "achieved_gbs": bps * 2 * S / (per / 1e3) / 1e9, "bytes_per_sample": bps}
-    res["bf16_speedup"] = res["fp32"]["kernel_ms_per_launch"] / res["bf16"]["kernel_ms_per_launch"]
+    if "fp32" in res and "bf16" in res:
+        res["bf16_speedup"] = res["fp32"]["kernel_ms_per_launch"] / res["bf16"]["kernel_ms_per_launch"]
     return res
 
 
@@ -371,6 +494,32 @@ def l2_flushed_variant(make, torch, p, q, launches=20):
     return res
 
 
+def l2_ceiling(gcp, torch, stream, d, Rp, S, reps=10, rows=1 << 15):
+    """Measured ceiling of the fused pass's model traffic: the same number
+    of row operations (S samples x d rows of Rp FP32 columns, each gathered
+    and each reduced with red.v4) on uniformly random rows of a 4 MB
+    L2-resident buffer, with no sampling, loss or hot rows.  Median of
+    `reps` launches per kind, CUDA events on the launching stream."""
+    buf = torch.zeros(rows * Rp, dtype=torch.float32, device="cuda")
+    out = {"rows": rows, "row_bytes": 4 * Rp, "ops": S, "rows_per_op": d}
+    for kind in ("red", "load", "both"):
+        for _ in range(3):
+            gcp.gcp_probe_l2(kind, buf, Rp, d, S, stream)
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gcp.gcp_probe_l2(kind, buf, Rp, d, S, stream)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        nbytes = S * d * 4 * Rp * (2 if kind == "both" else 1)
+        out[kind] = {"ms": ms, "gbs": nbytes / (ms / 1e3) / 1e9}
+    del buf
+    return out
+
+
 def combine_ranks(seconds, units_per_rank, world, dist=None, device="cpu"):
     """Whole-job throughput of N independent replicas: every rank processed
     units_per_rank units; the job took as long as its slowest rank (max over
@@ -384,7 +533,7 @@ def combine_ranks(seconds, units_per_rank, world, dist=None, device="cpu"):
     return world * units_per_rank / slowest, slowest
 
 
-def bernoulli_variant(gcp, torch, stream, launches=10):
+def bernoulli_variant(gcp, torch, stream, launches=10, with_oracle=True):
     """10000 x 10000 x 1000 binary tensor with 2e7 ones from a rank-16
     logistic generator, Bernoulli-logit loss, rank 64, 2^21 ones + 2^21
     zeros: gradient time with FP32 / BF16 factors and atomic /
@@ -401,6 +550,18 @@ def bernoulli_variant(gcp, torch, stream, launches=10):
     fac = synth.factors_normal(dims, 64, 2004, std=0.5)
     S = 1 << 21
     res = {"workload": "10000x10000x1000, 2e7 ones, Bernoulli-logit, rank 64, p=q=2^21"}
+    if with_oracle:
+        import oracle
+
+        skeys = oracle.sorted_keys(dims, w["coords"])
+
+        def run(n):
+            idx, x, wt, _ = oracle.stratified_samples(7, 5, n // 2, n - n // 2, dims, w["coords"], w["vals"],
+                                                      skeys=skeys)
+            oracle.sampled_loss_grad(dims, fac, "bernoulli", idx, x, wt)
+
+        res["cpu_oracle"] = oracle_rate(run)
+        del skeys
     for name, dtype, mttkrp in (("fp32_atomic", "fp32", "atomic"), ("bf16_atomic", "bf16", "atomic"),
                                 ("fp32_deterministic", "fp32", "deterministic")):
         ctx = gcp.gcp_create(dims, w["coords"], w["vals"], 64, "bernoulli", dtype=dtype, mttkrp=mttkrp, seed=7,
@@ -420,7 +581,7 @@ def bernoulli_variant(gcp, torch, stream, launches=10):
     return res
 
 
-def autograd_variant(gcp, torch, stream, steps=10):
+def autograd_variant(gcp, torch, stream, steps=10, with_oracle=True):
     """Dense 100x100x100x20x50 FP32 tensor (rank-8 sinusoidal CP signal +
     N(0, 0.1^2) noise), Gaussian loss, rank 16, 2^22 uniform samples:
     forward (sampled loss and, in the same fused pass, the gradient) +
@@ -432,8 +593,18 @@ def autograd_variant(gcp, torch, stream, steps=10):
     dims = [100, 100, 100, 20, 50]
     X = synth.dense_cp_sinusoid(dims, 1003, rank_true=8, sigma=0.1)
     ctx = gcp.gcp_create_dense(dims, X, 16, "gaussian", seed=3003, stream=stream)
+    fac = synth.factors_normal(dims, 16, 2003, std=0.5)
+    cpu = None
+    if with_oracle:
+        import oracle
+
+        def run(n):
+            idx, x, wt = oracle.uniform_samples(3003, 5, n, dims, X)
+            oracle.sampled_loss_grad(dims, fac, "gaussian", idx, x, wt)
+
+        cpu = oracle_rate(run)
     del X
-    A = [torch.tensor(a, device="cuda", requires_grad=True) for a in synth.factors_normal(dims, 16, 2003, std=0.5)]
+    A = [torch.tensor(a, device="cuda", requires_grad=True) for a in fac]
     s = 1 << 22
     loss = autograd.sampled_loss(ctx, 0, s, 0, A)
     loss.backward()
@@ -449,8 +620,11 @@ def autograd_variant(gcp, torch, stream, steps=10):
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
     ctx.close()
-    return {"workload": "dense 100x100x100x20x50, Gaussian, rank 16, 2^22 uniform samples",
-            "forward_backward_ms": ms, "samples_per_s": s / (ms / 1e3)}
+    out = {"workload": "dense 100x100x100x20x50, Gaussian, rank 16, 2^22 uniform samples",
+           "forward_backward_ms": ms, "samples_per_s": s / (ms / 1e3)}
+    if cpu:
+        out["cpu_oracle"] = cpu
+    return out
 
 
 def run_ours(args):
@@ -474,6 +648,19 @@ def run_ours(args):
     if dist:
         dist.barrier()
     gcp.load()
+    if args.only:  # profiling captures: one variant alone
+        stream = torch.cuda.current_stream()
+        fn = {"batched": batched_variant, "hbm": hbm_resident_variant, "nonfused": fused_vs_nonfused_variant,
+              "bernoulli": bernoulli_variant, "autograd": autograd_variant}.get(args.only)
+        if args.only == "l2probe":
+            res = l2_ceiling(gcp, torch, stream, 4, 32, 1 << 21)
+        else:
+            kw = {"dtypes": (args.dtype,)} if args.only == "hbm" else {}
+            if args.only in ("batched", "bernoulli", "autograd"):
+                kw["with_oracle"] = False
+            res = fn(gcp, torch, stream, **kw)
+        print(json.dumps({"variant": args.only, **res}), flush=True)
+        return
     if rank == 0:
         w = workload(args.nnz)
     if dist:
@@ -580,6 +767,18 @@ def run_ours(args):
                        "lts_sectors_pct_of_peak": measured_traffic("lts_sectors_pct_of_peak"),
                        "lts_throughput_pct_of_peak": measured_traffic("lts_throughput_pct_of_peak"),
                        "l1tex_throughput_pct_of_peak": measured_traffic("l1tex_throughput_pct_of_peak")}}
+    # the binding limit: the fused pass's gathers and reductions against the
+    # same row traffic measured alone on an L2-resident buffer
+    ceil = l2_ceiling(gcp, torch, stream, 4, 32, S)
+    red_bytes = S * 4 * 32 * 4
+    roofline["l2_rows"] = {
+        "what": "fused pass's factor-row gathers + gradient-row reductions (d=4 rows of 128 B each per sample) "
+                "vs the same row operations alone on uniformly random rows of an L2-resident buffer "
+                "(gcp_probe_l2, measured in this run)",
+        "achieved": 2 * red_bytes / kernel_avg_s / 1e9, "peak": ceil["both"]["gbs"], "unit": "GB/s",
+        "frac": (2 * red_bytes / kernel_avg_s / 1e9) / ceil["both"]["gbs"],
+        "reductions_achieved": red_bytes / kernel_avg_s / 1e9, "reductions_peak": ceil["red"]["gbs"],
+        "reductions_frac": (red_bytes / kernel_avg_s / 1e9) / ceil["red"]["gbs"], "probe": ceil}
     base = cpu_baseline(w)
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -618,6 +817,9 @@ def main():
                     help="nonzero count of a smaller tensor of the same shape (profiling captures)")
     ap.add_argument("--kernel-only", action="store_true", help="time the step loop only (profiling)")
     ap.add_argument("--no-variants", action="store_true", help="skip the batched and HBM-resident variants")
+    ap.add_argument("--only", default=None,
+                    choices=["batched", "hbm", "nonfused", "bernoulli", "autograd", "l2probe"],
+                    help="run one variant alone (profiling captures)")
     ap.add_argument("--dtype", default="fp32", choices=["fp32", "bf16"], help="factor storage for --kernel-only")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -291,8 +291,10 @@ gcp_status gcp_batch_tune(gcp_batch *batch, int32_t lane_cols, int32_t blocks);
 /* tau local steps of every client: step k (0-based) samples iteration
  * iter0 + k and applies Adam step t0 + k + 1 (Alg. 1) with prm.  Each client
  * ends with the same state as tau rounds of gcp_grad + gcp_adam_step on its
- * own context, up to the summation order of the atomic MTTKRP.
- * Asynchronous on the clients' stream. */
+ * own context, up to the summation order of the atomic MTTKRP.  A step is
+ * four launches in the graph: gradients cleared, the multi-client fused
+ * pass, one epilogue (loss finish, replica fold, Adam) and a counter advance.
+ * Asynchronous on the clients' stream; back-to-back calls need no sync. */
 gcp_status gcp_batch_local_steps(gcp_batch *batch, int32_t tau, const gcp_adam_params *prm, uint64_t iter0,
                                  int64_t t0);
 
@@ -345,6 +347,27 @@ gcp_status gcp_batch_server_step(gcp_batch *batch, const gcp_adam_params *prm, i
 gcp_status gcp_grad_samples_noalloc(int32_t ndim, const int64_t *dims, int32_t rank, int32_t loss,
                                     int64_t nsamples, const int32_t *idx, const float *x, const float *w,
                                     const float *A, float *G, double *loss_out, void *stream);
+
+/* Measured ceiling of the L2-resident row traffic (measurement support; the
+ * paper has no counterpart).  The fused pass's factor gathers and gradient
+ * reductions hit rows that stay in L2, so its binding limit is the SM -> L2
+ * path.  This call moves rows of buf in the same pattern and nothing else:
+ * ops operations, each by one group of row_floats/4 lanes, on rows_per_op
+ * uniformly random rows (splitmix64 of the op index):
+ *   GCP_PROBE_RED  adds a 16-byte slice per lane to each row
+ *                  (red.global.add.v4.f32, the atomic MTTKRP's scatter);
+ *   GCP_PROBE_LOAD reads each row with 16-byte vector loads (the gathers);
+ *   GCP_PROBE_BOTH reads rows_per_op rows, then adds to rows_per_op others.
+ * buf (device, caller-owned, 16-byte aligned, rows x row_floats floats,
+ * finite values) is modified by the RED and BOTH kinds with additions below
+ * 1e-29 per element.  row_floats a power of two in 4..128; rows_per_op in
+ * 1..8.  The caller times the call with events on `stream`.  GCP_ERR_ARG for
+ * bad sizes (message from gcp_last_error(NULL)).  Asynchronous. */
+#define GCP_PROBE_RED 0
+#define GCP_PROBE_LOAD 1
+#define GCP_PROBE_BOTH 2
+gcp_status gcp_probe_l2(int32_t kind, int32_t row_floats, int32_t rows_per_op, float *buf, int64_t rows,
+                        int64_t ops, void *stream);
 
 #ifdef __cplusplus
 }

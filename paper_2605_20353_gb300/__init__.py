@@ -102,6 +102,7 @@ SIGNATURES = {
     "gcp_batch_server_init": (_i32, [_vp]),
     "gcp_batch_server_step": (_i32, [_vp, ctypes.POINTER(gcp_adam_params), _i64]),
     "gcp_grad_samples_noalloc": (_i32, [_i32, _vp, _i32, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "gcp_probe_l2": (_i32, [_i32, _i32, _i32, _vp, _i64, _i64, _vp]),
 }
 
 
@@ -460,6 +461,23 @@ def gcp_grad_samples_noalloc(dims, rank, loss, idx, x, w, A, G, loss_out, stream
     _check(load().gcp_grad_samples_noalloc(len(d), d.ctypes.data, rank, LOSSES[loss], int(idx.shape[0]), _ptr(idx),
                                            _ptr(x), _ptr(w), _ptr(A), _ptr(G), _ptr(loss_out),
                                            _stream_handle(stream)), None)
+
+
+PROBES = {"red": 0, "load": 1, "both": 2}
+
+
+def gcp_probe_l2(kind, buf, row_floats, rows_per_op, ops, stream=None):
+    """Row traffic of the fused pass's pattern on an L2-resident buffer
+    (measurement support): `ops` groups of row_floats/4 lanes each reduce
+    into ("red"), read ("load") or read then reduce ("both") rows_per_op
+    random rows of buf, a device float32 tensor of rows x row_floats.
+    Asynchronous on `stream`; the caller times it."""
+    if buf.numel() % row_floats:
+        raise ValueError("buf must hold whole rows of row_floats floats")
+    _check_buf(buf, buf.numel(), "float32", "buf")
+    rows = buf.numel() // row_floats
+    _check(load().gcp_probe_l2(PROBES[kind], row_floats, rows_per_op, _ptr(buf), rows, int(ops),
+                               _stream_handle(stream)), None)
 
 
 # C-named conveniences over a context

@@ -95,6 +95,18 @@ def test_host_argument_checks_need_no_gpu(lib_path):
     assert h.value is None
 
 
+def test_l2_probe_rejects_bad_sizes_on_the_host(lib_path):
+    """The measurement probe checks its sizes before any CUDA call."""
+    import paper_2605_20353_gb300 as gcp
+
+    lib = gcp.load()
+    assert lib.gcp_probe_l2(3, 32, 4, 16, 1024, 1, None) == 1  # unknown kind
+    assert lib.gcp_probe_l2(0, 24, 4, 16, 1024, 1, None) == 1  # row not a power of two
+    assert b"power of two" in lib.gcp_last_error(None)
+    assert lib.gcp_probe_l2(0, 32, 9, 16, 1024, 1, None) == 1  # more rows per op than modes
+    assert lib.gcp_probe_l2(2, 32, 4, 8, 1024, 1, None) == 1  # unaligned buffer
+
+
 def test_fit_presets_are_valid_adam_settings():
     import paper_2605_20353_gb300 as gcp
 

@@ -601,3 +601,26 @@ def test_fit_restores_state_after_failed_epochs(env):
     for a, b in zip(ctx.get_factors(), F0):
         assert np.array_equal(a, b)
     ctx.close()
+
+
+def test_l2_probe_performs_every_row_operation(env):
+    """The measured ceiling is only meaningful if the probe does its work:
+    every reduction lands (the buffer's total equals the sum of all added
+    values) and the load probe leaves the buffer unchanged."""
+    gcp, torch = env
+    Rp, d, ops, rows = 32, 4, 100_003, 4096
+    buf = torch.zeros(rows * Rp, dtype=torch.float32, device="cuda")
+    gcp.gcp_probe_l2("red", buf, Rp, d, ops)
+    torch.cuda.synchronize()
+    # op o adds 1e-30 (o mod 8) to each of the Rp columns of d rows
+    k = np.arange(ops) % 8
+    expect = d * Rp * 1e-30 * float(k.sum())
+    total = float(buf.double().sum())
+    assert abs(total - expect) <= 1e-4 * expect, (total, expect)
+    before = buf.clone()
+    gcp.gcp_probe_l2("load", buf, Rp, d, ops)
+    torch.cuda.synchronize()
+    assert torch.equal(buf, before)
+    gcp.gcp_probe_l2("both", buf, 16, 3, ops)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(buf).all()) and float(buf.double().sum()) > total
