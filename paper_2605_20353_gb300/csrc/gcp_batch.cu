@@ -39,7 +39,8 @@ constexpr int kSpecWords = (int)((sizeof(gcpk::FusedSpec) + 15) / 16);  // 16-by
 struct ClientAux {
     float *A, *B, *C, *G, *Grep;
     void *Abf;
-    const int *hot_row;
+    const int *hot_row;   // replica slot -> row
+    const int *hot_slot;  // row -> replica slot, or -1
     int Htot;
     int64_t nparam;  // total_rows * Rp
     int R, Rp;
@@ -278,40 +279,52 @@ __global__ void __launch_bounds__(kThreads) k_batch_fused(const int4 *__restrict
 // ------------------------------------------------- per-client small kernels
 // grid.y = client; blocks of grid.x stride over that client's elements.
 // G = 0, one 16-byte quad per thread and step (nparam is a multiple of 4).
-__global__ void k_batch_zero(const ClientAux *__restrict__ aux) {
-    const ClientAux &a = aux[blockIdx.y];
-    float4 *G = reinterpret_cast<float4 *>(a.G);
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (a.nparam >> 2);
-         e += (int64_t)gridDim.x * blockDim.x)
-        G[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+// Adam constants in device memory: adam[0..4] = lr, beta1, beta2, eps, lower
+// (Alg. 1); adam[5..6] = the bias corrections 1/(1 - beta1^t) and
+// 1/(1 - beta2^t) of the step t = step[1] + 1 about to run; adam[7..8] =
+// beta1^t and beta2^t, advanced by one multiplication per step.
+__device__ __forceinline__ void set_bias_corrections(double *adam, double p1, double p2) {
+    adam[7] = p1;
+    adam[8] = p2;
+    adam[5] = 1.0 / (1.0 - p1);
+    adam[6] = 1.0 / (1.0 - p2);
 }
 
-// G(hot row) += sum of the replicas (all loads first), replicas cleared.
-__global__ void k_batch_fold(const ClientAux *__restrict__ aux) {
-    const ClientAux &a = aux[blockIdx.y];
-    const int64_t n = (int64_t)a.Htot * a.Rp;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        float v[gcpk::kReplicas];
-#pragma unroll
-        for (int r = 0; r < gcpk::kReplicas; ++r) v[r] = a.Grep[r * n + e];
-        float t = 0.0f;
-#pragma unroll
-        for (int r = 0; r < gcpk::kReplicas; ++r) t += v[r];
-#pragma unroll
-        for (int r = 0; r < gcpk::kReplicas; ++r) a.Grep[r * n + e] = 0.0f;
-        const int log2Rp = __ffs(a.Rp) - 1;  // Rp is a power of two
-        a.G[((int64_t)a.hot_row[e >> log2Rp] << log2Rp) + (e & (a.Rp - 1))] += t;
-    }
+// Counters and hyperparameters of one gcp_batch_local_steps call, passed as
+// kernel arguments so that back-to-back calls cannot see each other's values.
+__global__ void k_batch_set(uint64_t *step, double *adam, uint64_t iter0, uint64_t t0, double lr, double beta1,
+                            double beta2, double eps, double lower) {
+    step[0] = iter0;
+    step[1] = t0;
+    adam[0] = lr;
+    adam[1] = beta1;
+    adam[2] = beta2;
+    adam[3] = eps;
+    adam[4] = lower;
+    set_bias_corrections(adam, pow(beta1, (double)(t0 + 1)), pow(beta2, (double)(t0 + 1)));
 }
 
-// One block per client: its tiles' loss sums in fixed order, weighted.
-__global__ void k_batch_finish(const ClientAux *__restrict__ aux, const float2 *__restrict__ tile_loss,
-                               double *client_loss) {
-    const ClientAux &a = aux[blockIdx.x];
+// Block-wide, fixed-order sum of client a's per-tile loss partials, weighted
+// (FP64).  Each thread adds its tiles t, t + kThreads, ... in that order; eight
+// loads are issued before their adds so the chain does not wait on each one.
+__device__ __forceinline__ void finish_client_loss(const ClientAux &a, const float2 *__restrict__ tile_loss,
+                                                   double *out) {
     __shared__ double sh[2][kThreads];
     double nz = 0.0, z = 0.0;
-    for (int t = threadIdx.x; t < a.ntiles; t += kThreads) {
-        const float2 v = tile_loss[a.tile0 + t];
+    const float2 *tl = tile_loss + a.tile0;
+    int t = threadIdx.x;
+    for (; t + 7 * kThreads < a.ntiles; t += 8 * kThreads) {
+        float2 v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = tl[t + r * kThreads];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            nz += v[r].x;
+            z += v[r].y;
+        }
+    }
+    for (; t < a.ntiles; t += kThreads) {
+        const float2 v = tl[t];
         nz += v.x;
         z += v.y;
     }
@@ -325,61 +338,124 @@ __global__ void k_batch_finish(const ClientAux *__restrict__ aux, const float2 *
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) client_loss[blockIdx.x] = a.w_nz * sh[0][0] + a.w_z * sh[1][0];
+    if (threadIdx.x == 0) *out = a.w_nz * sh[0][0] + a.w_z * sh[1][0];
 }
 
-// Algorithm 1 for every client; t = step[1] + 1; hyperparameters in adam[5]
-// (lr, beta1, beta2, eps, lower).  Padded columns stay zero.
-__global__ void k_batch_adam(const ClientAux *__restrict__ aux, const double *__restrict__ adam,
-                             const uint64_t *__restrict__ step) {
-    const ClientAux &a = aux[blockIdx.y];
-    __shared__ float c[7];
-    if (threadIdx.x == 0) {
-        const double t = (double)(step[1] + 1);
-        c[0] = (float)adam[0];
-        c[1] = (float)adam[1];
-        c[2] = (float)adam[2];
-        c[3] = (float)(1.0 / (1.0 - pow(adam[1], t)));
-        c[4] = (float)(1.0 / (1.0 - pow(adam[2], t)));
-        c[5] = (float)adam[3];
-        c[6] = (float)adam[4];
-    }
-    __syncthreads();
-    // one 16-byte quad of A, B, C and G per thread and step: nparam and Rp
-    // are multiples of 4 and Rp is a power of two, so a quad lies in one row
-    uint2 *Abf = static_cast<uint2 *>(a.Abf);
-    const int cmask = a.Rp - 1;
-    for (int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; qi < (a.nparam >> 2);
-         qi += (int64_t)gridDim.x * blockDim.x) {
-        const int col = (int)((qi << 2) & cmask);
-        if (col >= a.R) continue;  // a padded quad stays zero
-        const float4 g4 = reinterpret_cast<const float4 *>(a.G)[qi];
-        float4 b4 = reinterpret_cast<const float4 *>(a.B)[qi];
-        float4 c4 = reinterpret_cast<const float4 *>(a.C)[qi];
-        float4 x4 = reinterpret_cast<const float4 *>(a.A)[qi];
-        const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
-        float bv[4] = {b4.x, b4.y, b4.z, b4.w}, cv[4] = {c4.x, c4.y, c4.z, c4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
+// Algorithm 1 on one 16-byte quad (4 entries of one row, columns col..col+3)
+// with its gradient g4; entries in padded columns stay zero.
+struct AdamConsts {
+    float lr, beta1, beta2, eps, lower, c1inv, c2inv;
+};
+
+__device__ __forceinline__ void adam_quad(const ClientAux &a, int64_t qi, int col, float4 g4, float4 b4, float4 c4,
+                                          float4 x4, const AdamConsts &k) {
+    const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+    float bv[4] = {b4.x, b4.y, b4.z, b4.w}, cv[4] = {c4.x, c4.y, c4.z, c4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (col + j >= a.R) continue;  // padded columns stay zero
-            const float g = gv[j];
-            bv[j] = c[1] * bv[j] + (1.0f - c[1]) * g;
-            cv[j] = c[2] * cv[j] + (1.0f - c[2]) * g * g;
-            xv[j] = fmaxf(xv[j] - c[0] * ((bv[j] * c[3]) / sqrtf(cv[j] * c[4] + c[5])), c[6]);
-        }
-        reinterpret_cast<float4 *>(a.B)[qi] = make_float4(bv[0], bv[1], bv[2], bv[3]);
-        reinterpret_cast<float4 *>(a.C)[qi] = make_float4(cv[0], cv[1], cv[2], cv[3]);
-        reinterpret_cast<float4 *>(a.A)[qi] = make_float4(xv[0], xv[1], xv[2], xv[3]);
-        if (Abf) {
-            const __nv_bfloat162 lo = __floats2bfloat162_rn(xv[0], xv[1]), hi = __floats2bfloat162_rn(xv[2], xv[3]);
-            Abf[qi] = make_uint2(*reinterpret_cast<const unsigned *>(&lo), *reinterpret_cast<const unsigned *>(&hi));
-        }
+    for (int j = 0; j < 4; ++j) {
+        if (col + j >= a.R) continue;  // padded columns stay zero
+        const float g = gv[j];
+        bv[j] = k.beta1 * bv[j] + (1.0f - k.beta1) * g;
+        cv[j] = k.beta2 * cv[j] + (1.0f - k.beta2) * g * g;
+        xv[j] = fmaxf(xv[j] - k.lr * ((bv[j] * k.c1inv) / sqrtf(cv[j] * k.c2inv + k.eps)), k.lower);
+    }
+    reinterpret_cast<float4 *>(a.B)[qi] = make_float4(bv[0], bv[1], bv[2], bv[3]);
+    reinterpret_cast<float4 *>(a.C)[qi] = make_float4(cv[0], cv[1], cv[2], cv[3]);
+    reinterpret_cast<float4 *>(a.A)[qi] = make_float4(xv[0], xv[1], xv[2], xv[3]);
+    if (a.Abf) {
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(xv[0], xv[1]), hi = __floats2bfloat162_rn(xv[2], xv[3]);
+        static_cast<uint2 *>(a.Abf)[qi] =
+            make_uint2(*reinterpret_cast<const unsigned *>(&lo), *reinterpret_cast<const unsigned *>(&hi));
     }
 }
 
-__global__ void k_batch_advance(uint64_t *step) {
+// Hot row: add its kReplicas replica quads to g4 in replica order, then
+// clear them for the next step.
+__device__ __forceinline__ void fold_quad(const ClientAux &a, int hs, int col, float4 &g4) {
+    const int64_t plane4 = ((int64_t)a.Htot * a.Rp) >> 2, o = ((int64_t)hs * a.Rp + col) >> 2;
+    float4 *R4 = reinterpret_cast<float4 *>(a.Grep);
+    for (int r0 = 0; r0 < gcpk::kReplicas; r0 += 8) {
+        float4 v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = R4[(r0 + r) * plane4 + o];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            g4.x += v[r].x;
+            g4.y += v[r].y;
+            g4.z += v[r].z;
+            g4.w += v[r].w;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) R4[(r0 + r) * plane4 + o] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+}
+
+// The epilogue of one local step of every client, one launch over a chunk
+// list built at batch creation.  A chunk {client, -1} finishes that client's
+// loss; a chunk {client, q} takes the client's parameter quads q ..
+// q + kPostQuads - 1, two per thread with all gradient loads issued first:
+// the gradient quad plus, for a hot row, its replica quads (replicas
+// cleared), then Algorithm 1 on the four entries.  G itself is cleared at
+// the start of the next step, just before the fused pass, so that its lines
+// are still in L2 when the reductions arrive.
+constexpr int kPostQuads = 2 * kThreads;
+
+__global__ void __launch_bounds__(kThreads, 4) k_batch_post(const ClientAux *__restrict__ aux,
+                                                            const int2 *__restrict__ chunks,
+                                                            const float2 *__restrict__ tile_loss, double *client_loss,
+                                                            const double *__restrict__ adam) {
+    const int2 ch = chunks[blockIdx.x];
+    const ClientAux &a = aux[ch.x];
+    if (ch.y < 0) {
+        finish_client_loss(a, tile_loss, client_loss + ch.x);
+        return;
+    }
+    const AdamConsts k{(float)adam[0], (float)adam[1], (float)adam[2], (float)adam[3],
+                       (float)adam[4], (float)adam[5], (float)adam[6]};
+    const int log2Rp = __ffs(a.Rp) - 1;  // Rp is a power of two and a multiple of 4
+    const int64_t nq = a.nparam >> 2;
+    const int64_t q[2] = {(int64_t)ch.y + threadIdx.x, (int64_t)ch.y + threadIdx.x + kThreads};
+    const float4 *G4 = reinterpret_cast<const float4 *>(a.G);
+    float4 g4[2];
+    int col[2], hs[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        col[u] = (int)((q[u] << 2) & (a.Rp - 1));
+        hs[u] = -1;
+        if (q[u] < nq) {
+            g4[u] = G4[q[u]];
+            if (a.hot_slot) hs[u] = __ldg(a.hot_slot + ((q[u] << 2) >> log2Rp));
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (hs[u] >= 0) fold_quad(a, hs[u], col[u], g4[u]);
+    float4 b4[2], c4[2], x4[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (q[u] < nq && col[u] < a.R) {
+            b4[u] = reinterpret_cast<const float4 *>(a.B)[q[u]];
+            c4[u] = reinterpret_cast<const float4 *>(a.C)[q[u]];
+            x4[u] = reinterpret_cast<const float4 *>(a.A)[q[u]];
+        }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (q[u] < nq && col[u] < a.R) adam_quad(a, q[u], col[u], g4[u], b4[u], c4[u], x4[u], k);
+}
+
+// Gradients cleared before the fused pass (grid.y = client).
+__global__ void k_batch_zero(const ClientAux *__restrict__ aux) {
+    const ClientAux &a = aux[blockIdx.y];
+    float4 *G = reinterpret_cast<float4 *>(a.G);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (a.nparam >> 2);
+         e += (int64_t)gridDim.x * blockDim.x)
+        G[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+__global__ void k_batch_advance(uint64_t *step, double *adam) {
     step[0] += 1;
     step[1] += 1;
+    set_bias_corrections(adam, adam[7] * adam[1], adam[8] * adam[2]);
 }
 
 // ------------------------------------------------------ GCP-FedAdam server
@@ -472,13 +548,13 @@ struct gcp_batch {
     int cols = 4, blocks = 0;        // tuning knobs: columns per lane, fused-kernel grid
     int4 *specs = nullptr;           // n x kSpecWords
     int *tile_start = nullptr;       // n + 1
+    int2 *chunks = nullptr;          // epilogue work list: {client, -1} loss, {client, first quad} Adam
+    int nchunks = 0;
     gcpb::ClientAux *aux = nullptr;  // n
     float2 *tile_loss = nullptr;     // total_tiles
     double *client_loss = nullptr;   // n
     uint64_t *step = nullptr;        // [0] iteration of the next gradient, [1] Adam steps done
-    double *adam = nullptr;          // lr, beta1, beta2, eps, lower
-    uint64_t *h_step = nullptr;      // pinned staging
-    double *h_adam = nullptr;
+    double *adam = nullptr;          // lr, beta1, beta2, eps, lower, bias corrections, beta powers
     double *h_loss = nullptr;
     int64_t max_param = 0, max_rep = 0;
     cudaStream_t st = nullptr, user_st = nullptr;
@@ -514,13 +590,12 @@ void batch_free(gcp_batch *b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaFree(b->specs);
     cudaFree(b->tile_start);
+    cudaFree(b->chunks);
     cudaFree(b->aux);
     cudaFree(b->tile_loss);
     cudaFree(b->client_loss);
     cudaFree(b->step);
     cudaFree(b->adam);
-    cudaFreeHost(b->h_step);
-    cudaFreeHost(b->h_adam);
     cudaFreeHost(b->h_loss);
     cudaFree(b->U);
     cudaFree(b->Bs);
@@ -571,18 +646,16 @@ cudaError_t launch_batch_fused(const gcp_batch *b) {
     }
 }
 
-// One local step of every client, enqueued on b->st (also used for capture).
+// One local step of every client, enqueued on b->st (also used for capture):
+// gradients cleared, the multi-client fused pass, one epilogue launch, the
+// counter advance.
 gcp_status enqueue_step(gcp_batch *b) {
     const int nb = gcpb::kThreads;
-    const dim3 gp((unsigned)std::min<int64_t>(64, (b->max_param + nb - 1) / nb), (unsigned)b->n);
-    const dim3 gr((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (b->max_rep + nb - 1) / nb)), (unsigned)b->n);
+    const dim3 gp((unsigned)std::min<int64_t>(64, (b->max_param / 4 + nb - 1) / nb), (unsigned)b->n);
     gcpb::k_batch_zero<<<gp, nb, 0, b->st>>>(b->aux);
-    BCUDA(b, cudaGetLastError());
     BCUDA(b, launch_batch_fused(b));
-    if (b->max_rep > 0) gcpb::k_batch_fold<<<gr, nb, 0, b->st>>>(b->aux);
-    gcpb::k_batch_finish<<<b->n, nb, 0, b->st>>>(b->aux, b->tile_loss, b->client_loss);
-    gcpb::k_batch_adam<<<gp, nb, 0, b->st>>>(b->aux, b->adam, b->step);
-    gcpb::k_batch_advance<<<1, 1, 0, b->st>>>(b->step);
+    gcpb::k_batch_post<<<b->nchunks, nb, 0, b->st>>>(b->aux, b->chunks, b->tile_loss, b->client_loss, b->adam);
+    gcpb::k_batch_advance<<<1, 1, 0, b->st>>>(b->step, b->adam);
     BCUDA(b, cudaGetLastError());
     return GCP_OK;
 }
@@ -647,6 +720,7 @@ gcp_status gcp_batch_create(int32_t nclients, gcp_ctx *const *clients, const int
         a.Grep = c->Grep;
         a.Abf = c->Abf;
         a.hot_row = c->hot_row;
+        a.hot_slot = c->hot_slot;
         a.Htot = c->Htot;
         a.nparam = c->total_rows * c->Rp;
         a.R = c->R;
@@ -658,11 +732,18 @@ gcp_status gcp_batch_create(int32_t nclients, gcp_ctx *const *clients, const int
         b->max_param = std::max<int64_t>(b->max_param, a.nparam);
         b->max_rep = std::max<int64_t>(b->max_rep, (int64_t)a.Htot * a.Rp);
     }
+    std::vector<int2> chunks;  // loss chunks first, so they start with the first wave
+    for (int i = 0; i < nclients; ++i) chunks.push_back(make_int2(i, -1));
+    for (int i = 0; i < nclients; ++i)
+        for (int64_t q0 = 0; q0 < aux[i].nparam / 4; q0 += gcpb::kPostQuads) chunks.push_back(make_int2(i, (int)q0));
+    b->nchunks = (int)chunks.size();
     cudaError_t e;
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(b->device);
     if ((e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking)) ||
+        (e = cudaMalloc(&b->chunks, chunks.size() * sizeof(int2))) ||
+        (e = cudaMemcpy(b->chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice)) ||
         (e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming)) ||
         (e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming)) ||
         (e = cudaMalloc(&b->specs, specs.size() * sizeof(int4))) ||
@@ -670,9 +751,7 @@ gcp_status gcp_batch_create(int32_t nclients, gcp_ctx *const *clients, const int
         (e = cudaMalloc(&b->aux, aux.size() * sizeof(gcpb::ClientAux))) ||
         (e = cudaMalloc(&b->tile_loss, (size_t)std::max(1, b->total_tiles) * sizeof(float2))) ||
         (e = cudaMalloc(&b->client_loss, (size_t)nclients * sizeof(double))) ||
-        (e = cudaMalloc(&b->step, 2 * sizeof(uint64_t))) || (e = cudaMalloc(&b->adam, 5 * sizeof(double))) ||
-        (e = cudaMallocHost(&b->h_step, 2 * sizeof(uint64_t))) ||
-        (e = cudaMallocHost(&b->h_adam, 5 * sizeof(double))) ||
+        (e = cudaMalloc(&b->step, 2 * sizeof(uint64_t))) || (e = cudaMalloc(&b->adam, 9 * sizeof(double))) ||
         (e = cudaMallocHost(&b->h_loss, (size_t)nclients * sizeof(double))) ||
         (e = cudaMemcpy(b->specs, specs.data(), specs.size() * sizeof(int4), cudaMemcpyHostToDevice)) ||
         (e = cudaMemcpy(b->tile_start, tstart.data(), tstart.size() * sizeof(int), cudaMemcpyHostToDevice)) ||
@@ -741,18 +820,13 @@ gcp_status gcp_batch_local_steps(gcp_batch *b, int32_t tau, const gcp_adam_param
         b->graph_cols = b->cols;
         b->graph_blocks = b->blocks;
     }
-    b->h_step[0] = iter0;
-    b->h_step[1] = (uint64_t)t0;
-    b->h_adam[0] = prm->lr;
-    b->h_adam[1] = prm->beta1;
-    b->h_adam[2] = prm->beta2;
-    b->h_adam[3] = prm->eps;
-    b->h_adam[4] = prm->lower;
     BCUDA(b, cudaEventRecord(b->ev_in, b->user_st));  // after the clients' earlier work
     BCUDA(b, cudaStreamWaitEvent(b->st, b->ev_in, 0));
-    BCUDA(b, cudaMemcpyAsync(b->step, b->h_step, 2 * sizeof(uint64_t), cudaMemcpyHostToDevice, b->st));
-    BCUDA(b, cudaMemcpyAsync(b->adam, b->h_adam, 5 * sizeof(double), cudaMemcpyHostToDevice, b->st));
+    gcpb::k_batch_set<<<1, 1, 0, b->st>>>(b->step, b->adam, iter0, (uint64_t)t0, prm->lr, prm->beta1, prm->beta2,
+                                          prm->eps, prm->lower);
+    BCUDA(b, cudaGetLastError());
     BCUDA(b, cudaGraphLaunch(b->graph, b->st));
+    for (gcp_ctx *c : b->clients) c->g_clear = false;  // G holds the last local step's gradient
     BCUDA(b, cudaEventRecord(b->ev_out, b->st));  // the clients' later work waits for the steps
     BCUDA(b, cudaStreamWaitEvent(b->user_st, b->ev_out, 0));
     if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
