@@ -230,3 +230,47 @@ def test_fedadam_requires_one_model_shape(env, shards):
     with pytest.raises(gcp.GcpError):
         b.server_step(gcp.AdamParams(), 1)
     b.close()
+
+
+def test_batch_padded_rank_empty_client_and_unreplicated_modes(env):
+    """Rank 6 (rows padded to 8 columns), a client with no samples, and a
+    client whose first mode has more rows than the replica threshold: two
+    local steps of the batch equal two gcp_grad + gcp_adam_step rounds of
+    each client alone, and the empty client's loss is 0."""
+    gcp, torch = env
+    adam = gcp.AdamParams(**ADAM)
+    specs = [([700, 40, 30], 5000, 600, 650), ([50, 60, 70], 4000, 500, 480), ([45, 35, 25], 900, 0, 0)]
+    shards = []
+    for i, (dims, nnz, p, q) in enumerate(specs):
+        coords, vals = synth.uniform_sparse(dims, nnz, 8100 + i, lam=2.0)
+        f = synth.factors_uniform(dims, 6, 8200 + i, lo=0.1, hi=1.0)
+        shards.append(dict(dims=dims, coords=coords, vals=vals, factors=f, p=p, q=q, seed=8300 + i))
+
+    def mk():
+        out = []
+        for s in shards:
+            c = gcp.gcp_create(s["dims"], s["coords"], s["vals"], 6, "poisson", seed=s["seed"])
+            c.set_factors(s["factors"])
+            out.append(c)
+        return out
+
+    ref = mk()
+    last = []
+    for c, s in zip(ref, shards):
+        for k in range(2):
+            L, _ = c.grad(11 + k, s["p"], s["q"])
+            c.adam_step(adam, k + 1)
+        last.append(L)
+    bat = mk()
+    b = gcp.GcpBatch(bat, [s["p"] for s in shards], [s["q"] for s in shards])
+    b.local_steps(2, adam, 11, 0)
+    losses = b.losses()
+    for c, r, L, Lr in zip(bat, ref, losses, last):
+        A = np.concatenate([a.ravel() for a in c.get_factors()])
+        Ar = np.concatenate([a.ravel() for a in r.get_factors()])
+        assert rel_err(A, Ar) <= 1e-5
+        assert L == pytest.approx(Lr, rel=1e-6, abs=0.0)
+    assert losses[2] == 0.0
+    b.close()
+    for c in ref + bat:
+        c.close()
