@@ -49,14 +49,16 @@ __global__ void k_radix_hist(const int32_t *__restrict__ keys, int key_stride, i
 
 // Scan phases: each block of kScanBlock elements scans itself in place and
 // records its total; one block scans the totals (and writes the grand total).
-__global__ void k_scan_blocks(int32_t *a, int64_t n, int32_t *block_sums) {
+// in = out scans in place; with `flags`, the input is a carry-key array and
+// each element counts 1 if its key is set (>= 0), else 0.
+__global__ void k_scan_blocks(const int32_t *in, int32_t *out, int64_t n, int32_t *block_sums, bool flags) {
     __shared__ int32_t warp_tot[kT / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * (kScanBlock / kT);
     int32_t v[kScanBlock / kT];
     int32_t sum = 0;
 #pragma unroll
     for (int j = 0; j < kScanBlock / kT; ++j) {
-        v[j] = base + j < n ? a[base + j] : 0;
+        v[j] = base + j < n ? (flags ? (in[base + j] >= 0 ? 1 : 0) : in[base + j]) : 0;
         sum += v[j];
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -76,7 +78,7 @@ __global__ void k_scan_blocks(int32_t *a, int64_t n, int32_t *block_sums) {
     int32_t run = before + incl - sum;
 #pragma unroll
     for (int j = 0; j < kScanBlock / kT; ++j) {
-        if (base + j < n) a[base + j] = run;
+        if (base + j < n) out[base + j] = run;
         run += v[j];
     }
     if (threadIdx.x == 0) block_sums[blockIdx.x] = block_total;
@@ -108,40 +110,75 @@ __global__ void k_scan_top(int32_t *a, int64_t n, int32_t *total) {
     }
 }
 
-// Exclusive prefix sum of n ints, left in two parts: a[i] holds the scan
+// Exclusive prefix sum of n ints (of `in`, or of the set flags of a carry-key
+// array), left in two parts: a[i] holds the scan
 // within its block of kScanBlock elements and block_sums[i / kScanBlock]
 // the scan of the block totals, so the full value is their sum (consumers
 // add the two).  *total (if not NULL) receives the grand total.
-void scan_two_part(int32_t *a, int64_t n, int32_t *total, int32_t *block_sums, cudaStream_t st) {
+void scan_two_part(const int32_t *in, int32_t *a, int64_t n, bool flags, int32_t *total, int32_t *block_sums,
+                   cudaStream_t st) {
     const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
-    k_scan_blocks<<<(unsigned)nb, kT, 0, st>>>(a, n, block_sums);
+    k_scan_blocks<<<(unsigned)nb, kT, 0, st>>>(in, a, n, block_sums, flags);
     k_scan_top<<<1, kT, 0, st>>>(block_sums, nb, total);
 }
 
-// Stable scatter of one 8-bit digit pass.  Keys of a tile are ranked in
-// index order: rounds of kT keys, warps in order, lanes in order.
-__global__ void k_radix_scatter(const int32_t *__restrict__ keys, int key_stride, const int32_t *__restrict__ vals,
-                                int64_t n, int shift, const int32_t *__restrict__ offsets,
-                                const int32_t *__restrict__ offset_blocks, int ntiles,
-                                int32_t *__restrict__ keys_out, int32_t *__restrict__ vals_out) {
-    __shared__ int running[256];
+// Stable scatter of one 8-bit digit pass.  The tile's keys are first ranked
+// into shared memory in index order (rounds of kT keys, warps in order,
+// lanes in order), which leaves the tile sorted by digit; the sorted tile is
+// then written out in order, so consecutive threads store consecutive
+// positions of a digit's run and the global writes are coalesced.
+constexpr int kKeysPerThread = kTile / kT;
+
+__global__ void __launch_bounds__(kT) k_radix_scatter(const int32_t *__restrict__ keys, int key_stride,
+                                                      const int32_t *__restrict__ vals, int64_t n, int shift,
+                                                      const int32_t *__restrict__ offsets,
+                                                      const int32_t *__restrict__ offset_blocks, int ntiles,
+                                                      int32_t *__restrict__ keys_out, int32_t *__restrict__ vals_out) {
+    __shared__ int32_t s_key[kTile], s_val[kTile];
+    __shared__ int running[256];  // next local position of each digit
+    __shared__ int gshift[256];   // global position - local position, per digit
     __shared__ int wcount[kT / 32][256];
+    __shared__ int wsum[kT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t oi = (int64_t)threadIdx.x * ntiles + blockIdx.x;  // thread = digit
-    running[threadIdx.x] = offsets[oi] + offset_blocks[oi / kScanBlock];
+    const int64_t first = (int64_t)blockIdx.x * kTile;
+    const int tile_n = n - first < kTile ? (int)(n - first) : kTile;
+    int32_t key[kKeysPerThread], val[kKeysPerThread];
+    running[threadIdx.x] = 0;
     for (int w = 0; w < kT / 32; ++w) wcount[w][threadIdx.x] = 0;
     __syncthreads();
-    const int64_t first = (int64_t)blockIdx.x * kTile;
-    for (int r = 0; r < kTile / kT; ++r) {
-        const int64_t i = first + r * kT + threadIdx.x;
-        const bool valid = i < n;
-        int32_t key = 0, val = 0;
-        int digit = 256;  // no digit: never matches a real one
-        if (valid) {
-            key = keys[i * key_stride];
-            val = vals ? vals[i] : (int32_t)i;
-            digit = (key >> shift) & 255;
+#pragma unroll
+    for (int r = 0; r < kKeysPerThread; ++r) {
+        const int i = r * kT + threadIdx.x;
+        key[r] = 0;
+        val[r] = 0;
+        if (i < tile_n) {
+            key[r] = keys[(first + i) * key_stride];
+            val[r] = vals ? vals[first + i] : (int32_t)(first + i);
+            atomicAdd(&running[(key[r] >> shift) & 255], 1);  // the tile's digit counts
         }
+    }
+    __syncthreads();
+    // exclusive scan of the 256 digit counts (thread = digit)
+    const int cnt = running[threadIdx.x];
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    const int local_start = before + incl - cnt;
+    const int64_t oi = (int64_t)threadIdx.x * ntiles + blockIdx.x;
+    gshift[threadIdx.x] = offsets[oi] + offset_blocks[oi / kScanBlock] - local_start;
+    running[threadIdx.x] = local_start;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kKeysPerThread; ++r) {
+        const bool valid = r * kT + (int)threadIdx.x < tile_n;
+        const int digit = valid ? (key[r] >> shift) & 255 : 256;  // 256 never matches a real digit
         const unsigned peers = __match_any_sync(0xFFFFFFFFu, digit);
         const int rank = __popc(peers & ((1u << lane) - 1u));
         if (valid && rank == 0) wcount[warp][digit] = __popc(peers);
@@ -149,8 +186,8 @@ __global__ void k_radix_scatter(const int32_t *__restrict__ keys, int key_stride
         if (valid) {
             int pos = running[digit] + rank;
             for (int w = 0; w < warp; ++w) pos += wcount[w][digit];
-            keys_out[pos] = key;
-            vals_out[pos] = val;
+            s_key[pos] = key[r];
+            s_val[pos] = val[r];
         }
         __syncthreads();
         int add = 0;
@@ -160,6 +197,12 @@ __global__ void k_radix_scatter(const int32_t *__restrict__ keys, int key_stride
         }
         running[threadIdx.x] += add;
         __syncthreads();
+    }
+    for (int i = threadIdx.x; i < tile_n; i += kT) {
+        const int32_t k = s_key[i];
+        const int pos = gshift[(k >> shift) & 255] + i;
+        keys_out[pos] = k;
+        vals_out[pos] = s_val[i];
     }
 }
 
@@ -179,6 +222,16 @@ template <typename TF, int NQ>
 __device__ __forceinline__ void load_cols(const TF *F, int off, const int (&col)[NQ], float (&o)[4 * NQ]) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q) Quad<TF>::load(F + off + col[q], o + 4 * q);
+}
+
+// Mark a chunk's carry slots that no run used (key -1), so the next level
+// needs no separate clearing pass.  A run touching both edges uses the left
+// slot only.
+__device__ __forceinline__ void clear_unused_slots(int32_t *ckey, int64_t chunk, bool left_used, bool right_used,
+                                                   int glane) {
+    if (glane != 0) return;
+    if (!left_used) ckey[2 * chunk] = -1;
+    if (!right_used) ckey[2 * chunk + 1] = -1;
 }
 
 // Emit one run of equal keys: a run inside the chunk is final (stored to G),
@@ -241,6 +294,7 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
         for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
         int cur = keys[lo];
         bool before = lo > 0 && keys[lo - 1] == cur;
+        const bool left = before;  // the chunk's left carry slot gets used
         for (int b = 0; b < len; b += L) {
             // this lane's position of the batch: key, y and the D-1 row
             // offsets of the other modes (mode k < n at j = k, k > n at k-1)
@@ -294,6 +348,7 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
         }
         const bool after = hi < n && keys[hi] == cur;
         emit_run<NQ>(P.G, P.Rp, rown, cur, acc, col, before, after, (int)c, ckey, cvec);
+        clear_unused_slots(ckey, c, left, after && !before, glane);
     }
 }
 
@@ -301,7 +356,7 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
 template <int COLS>
 __global__ void __launch_bounds__(kT) k_seg_vectors(const SegSpec P, const int32_t *__restrict__ keys,
                                                     const float *__restrict__ vecs, const int32_t *__restrict__ dn,
-                                                    int32_t *ckey, float *cvec) {
+                                                    int64_t nch_bound, int32_t *ckey, float *cvec) {
     constexpr int NQ = COLS / 4;
     const int lane = threadIdx.x & 31;
     const int L = 1 << P.log2L;
@@ -321,6 +376,7 @@ __global__ void __launch_bounds__(kT) k_seg_vectors(const SegSpec P, const int32
         for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
         int cur = keys[lo];
         bool before = lo > 0 && keys[lo - 1] == cur;
+        const bool left = before;
         for (int64_t i0 = lo; i0 < hi; i0 += kAhead) {
             // fetch kAhead positions' keys and vector slices, then add in order
             int key[kAhead];
@@ -353,18 +409,11 @@ __global__ void __launch_bounds__(kT) k_seg_vectors(const SegSpec P, const int32
         }
         const bool after = hi < n && keys[hi] == cur;
         emit_run<NQ>(P.G, P.Rp, rown, cur, acc, col, before, after, (int)c, ckey, cvec);
+        clear_unused_slots(ckey, c, left, after && !before, glane);
     }
-}
-
-__global__ void k_fill_int(int32_t *a, int64_t n, int32_t v) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        a[i] = v;
-}
-
-// flag[i] = 1 if carry slot i is used.
-__global__ void k_carry_flags(const int32_t *ckey, int64_t n, int32_t *flag) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        flag[i] = ckey[i] >= 0 ? 1 : 0;
+    // chunks between the list's length and the grid's bound carry nothing
+    for (int64_t c = nchunks + group; c < nch_bound; c += ngroups)
+        clear_unused_slots(ckey, c, false, false, glane);
 }
 
 // Order-preserving compaction of the used carry slots, one 16-byte quad of
@@ -522,7 +571,7 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
         int32_t *kout = kA, *vout = vA;
         for (int shift = 0; shift < bits; shift += 8) {
             k_radix_hist<<<(int)ntiles, kT, 0, st>>>(kin, kstride, S, shift, hist, (int)ntiles);
-            scan_two_part(hist, 256 * ntiles, nullptr, bsum, st);
+            scan_two_part(hist, hist, 256 * ntiles, false, nullptr, bsum, st);
             k_radix_scatter<<<(int)ntiles, kT, 0, st>>>(kin, kstride, vin, S, shift, hist, bsum, (int)ntiles, kout,
                                                         vout);
             DET_CUDA(cudaGetLastError());
@@ -535,7 +584,6 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
         // 3. chunked segmented reduction, level 1 over samples
         int64_t nch = (S + kChunk - 1) / kChunk;
         const int grid = grid_for(nch * lanes, kT);
-        k_fill_int<<<grid_for(2 * nch, kT), kT, 0, st>>>(ckey_out, 2 * nch, -1);
         if (c->Abf)
             launch_seg_samples<__nv_bfloat16>(P, c->cols, grid, kin, vin, S, ckey_out, cvec_out, st);
         else
@@ -546,19 +594,19 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
         // (two carries per chunk of the previous level), so no host sync.
         int64_t nslots = 2 * nch;
         while (nch > 1) {
-            k_carry_flags<<<grid_for(nslots, kT), kT, 0, st>>>(ckey_out, nslots, cpos);
-            scan_two_part(cpos, nslots, dlen, bsum, st);
+            scan_two_part(ckey_out, cpos, nslots, true, dlen, bsum, st);
             k_carry_compact<<<grid_for(nslots * (c->Rp / 4), kT), kT, 0, st>>>(ckey_out, cvec_out, nslots, cpos,
                                                                                bsum, log2q, lkey, lvec);
             nch = (nslots + kChunk - 1) / kChunk;
             nslots = 2 * nch;
             std::swap(ckey_in, ckey_out);
             std::swap(cvec_in, cvec_out);
-            k_fill_int<<<grid_for(nslots, kT), kT, 0, st>>>(ckey_out, nslots, -1);
             if (c->cols == 8)
-                k_seg_vectors<8><<<grid_for(nch * lanes, kT), kT, 0, st>>>(P, lkey, lvec, dlen, ckey_out, cvec_out);
+                k_seg_vectors<8><<<grid_for(nch * lanes, kT), kT, 0, st>>>(P, lkey, lvec, dlen, nch, ckey_out,
+                                                                          cvec_out);
             else
-                k_seg_vectors<4><<<grid_for(nch * lanes, kT), kT, 0, st>>>(P, lkey, lvec, dlen, ckey_out, cvec_out);
+                k_seg_vectors<4><<<grid_for(nch * lanes, kT), kT, 0, st>>>(P, lkey, lvec, dlen, nch, ckey_out,
+                                                                          cvec_out);
             DET_CUDA(cudaGetLastError());
         }
     }
