@@ -578,6 +578,11 @@ def bernoulli_variant(gcp, torch, stream, launches=10, with_oracle=True):
         ms = e0.elapsed_time(e1) / launches
         res[name] = {"gradient_ms": ms, "samples_per_s": 2 * S / (ms / 1e3)}
         ctx.close()
+    # the same row traffic (3 rows of 256 B gathered and reduced per sample)
+    # alone on an L2-resident buffer: the atomic gradient's measured ceiling
+    ceil = l2_ceiling(gcp, torch, stream, 3, 64, 2 * S, reps=5)
+    res["l2_rows_probe_ms"] = ceil["both"]["ms"]
+    res["fp32_atomic"]["l2_rows_frac"] = ceil["both"]["ms"] / res["fp32_atomic"]["gradient_ms"]
     return res
 
 
@@ -610,6 +615,8 @@ def autograd_variant(gcp, torch, stream, steps=10, with_oracle=True):
     loss.backward()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    ctx.profile_read()
     e0.record(stream)
     for i in range(steps):
         for a in A:
@@ -618,10 +625,17 @@ def autograd_variant(gcp, torch, stream, steps=10, with_oracle=True):
         loss.backward()
     e1.record(stream)
     e1.synchronize()
+    kms, nl = ctx.profile_read()
+    ctx.profile(False)
     ms = e0.elapsed_time(e1) / steps
     ctx.close()
+    # the fused pass's row traffic (5 rows of 64 B gathered and reduced per
+    # sample) alone on an L2-resident buffer
+    ceil = l2_ceiling(gcp, torch, stream, 5, 16, s, reps=5)
+    fused_ms = kms / max(1, nl)
     out = {"workload": "dense 100x100x100x20x50, Gaussian, rank 16, 2^22 uniform samples",
-           "forward_backward_ms": ms, "samples_per_s": s / (ms / 1e3)}
+           "forward_backward_ms": ms, "samples_per_s": s / (ms / 1e3), "fused_kernel_ms": fused_ms,
+           "l2_rows_probe_ms": ceil["both"]["ms"], "l2_rows_frac": ceil["both"]["ms"] / fused_ms if nl else None}
     if cpu:
         out["cpu_oracle"] = cpu
     return out

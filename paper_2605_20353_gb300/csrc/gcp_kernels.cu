@@ -493,13 +493,13 @@ __global__ void k_adam(int64_t n, int Rp, int R, float *__restrict__ A, float *_
     }
 }
 
-// One training step's epilogue after the fused pass, in one launch: block 0
-// first finishes the FP64 loss from the block partials (fixed order); then
-// every element of the flat parameter vector takes its gradient (adding the
-// replicas of a hot row and clearing them), applies Algorithm 1, and clears
-// G for the next step.
+// One training step's epilogue after the fused pass, in one launch: the last
+// block finishes the FP64 loss from the block partials (fixed order), while
+// the others take every element of the flat parameter vector: its gradient
+// (adding the replicas of a hot row and clearing them), Algorithm 1, and G
+// cleared for the next step.
 __global__ void __launch_bounds__(kThreads) k_post_step(PostSpec P) {
-    if (blockIdx.x == 0) {
+    if (blockIdx.x == gridDim.x - 1) {  // the last block only finishes the loss
         __shared__ double sh[3][kThreads];
         double t[3] = {0.0, 0.0, 0.0};
         for (int b = threadIdx.x; b < P.nblocks; b += kThreads)
@@ -517,37 +517,44 @@ __global__ void __launch_bounds__(kThreads) k_post_step(PostSpec P) {
             P.dloss[1] = sh[2][0];
             if (!isfinite(loss)) atomicOr(P.status, kErrNonfinite);
         }
+        return;
     }
     const int64_t plane = (int64_t)P.Htot * P.Rp;
     const int log2Rp = __ffs(P.Rp) - 1;  // Rp is a power of two
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < P.n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < P.n; e += stride) {
         const int row = (int)(e >> log2Rp), col = (int)(e & (P.Rp - 1));
+        // the gradient, the moments, the factor and the replica slot are
+        // independent loads, issued together
         float g = P.G[e];
+        const float b0 = P.B[e], c0 = P.C[e], a0 = P.A[e];
         const int hs = P.hot_slot ? __ldg(P.hot_slot + row) : -1;
-        if (hs >= 0) {  // all replica loads first, added in replica order, then cleared
-            float v[kReplicas];
+        if (hs >= 0) {  // replicas added in replica order, 16 loads in flight at a time, then cleared
             const int64_t o = (int64_t)hs * P.Rp + col;
+            for (int r0 = 0; r0 < kReplicas; r0 += 16) {
+                float v[16];
 #pragma unroll
-            for (int r = 0; r < kReplicas; ++r) v[r] = P.Grep[r * plane + o];
+                for (int r = 0; r < 16; ++r) v[r] = P.Grep[(r0 + r) * plane + o];
 #pragma unroll
-            for (int r = 0; r < kReplicas; ++r) g += v[r];
+                for (int r = 0; r < 16; ++r) g += v[r];
 #pragma unroll
-            for (int r = 0; r < kReplicas; ++r) P.Grep[r * plane + o] = 0.0f;
+                for (int r = 0; r < 16; ++r) P.Grep[(r0 + r) * plane + o] = 0.0f;
+            }
         }
         P.G[e] = 0.0f;
         if (col >= P.R) continue;
-        const float b = P.beta1 * P.B[e] + (1.0f - P.beta1) * g;
-        const float c = P.beta2 * P.C[e] + (1.0f - P.beta2) * g * g;
+        const float b = P.beta1 * b0 + (1.0f - P.beta1) * g;
+        const float c = P.beta2 * c0 + (1.0f - P.beta2) * g * g;
         P.B[e] = b;
         P.C[e] = c;
-        const float a = fmaxf(P.A[e] - P.lr * ((b * P.c1inv) / sqrtf(c * P.c2inv + P.eps)), P.lower);
+        const float a = fmaxf(a0 - P.lr * ((b * P.c1inv) / sqrtf(c * P.c2inv + P.eps)), P.lower);
         P.A[e] = a;
         if (P.Abf) static_cast<__nv_bfloat16 *>(P.Abf)[e] = __float2bfloat16_rn(a);
     }
 }
 
 cudaError_t launch_post_step(const PostSpec &p, cudaStream_t st) {
-    k_post_step<<<elementwise_blocks(p.n), kThreads, 0, st>>>(p);
+    k_post_step<<<elementwise_blocks(p.n) + 1, kThreads, 0, st>>>(p);  // + the loss block
     return cudaGetLastError();
 }
 

@@ -51,7 +51,10 @@ __global__ void k_radix_hist(const int32_t *__restrict__ keys, int key_stride, i
 // records its total; one block scans the totals (and writes the grand total).
 // in = out scans in place; with `flags`, the input is a carry-key array and
 // each element counts 1 if its key is set (>= 0), else 0.
-__global__ void k_scan_blocks(const int32_t *in, int32_t *out, int64_t n, int32_t *block_sums, bool flags) {
+// With one block (`total` not NULL), the block also finishes the two-part
+// scan: block_sums[0] = 0 and *total = the grand total.
+__global__ void k_scan_blocks(const int32_t *in, int32_t *out, int64_t n, int32_t *block_sums, bool flags,
+                              int32_t *total) {
     __shared__ int32_t warp_tot[kT / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * (kScanBlock / kT);
     int32_t v[kScanBlock / kT];
@@ -81,7 +84,14 @@ __global__ void k_scan_blocks(const int32_t *in, int32_t *out, int64_t n, int32_
         if (base + j < n) out[base + j] = run;
         run += v[j];
     }
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = block_total;
+    if (threadIdx.x == 0) {
+        if (gridDim.x == 1) {
+            block_sums[0] = 0;
+            if (total) *total = block_total;
+        } else {
+            block_sums[blockIdx.x] = block_total;
+        }
+    }
 }
 
 __global__ void k_scan_top(int32_t *a, int64_t n, int32_t *total) {
@@ -118,8 +128,8 @@ __global__ void k_scan_top(int32_t *a, int64_t n, int32_t *total) {
 void scan_two_part(const int32_t *in, int32_t *a, int64_t n, bool flags, int32_t *total, int32_t *block_sums,
                    cudaStream_t st) {
     const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
-    k_scan_blocks<<<(unsigned)nb, kT, 0, st>>>(in, a, n, block_sums, flags);
-    k_scan_top<<<1, kT, 0, st>>>(block_sums, nb, total);
+    k_scan_blocks<<<(unsigned)nb, kT, 0, st>>>(in, a, n, block_sums, flags, total);
+    if (nb > 1) k_scan_top<<<1, kT, 0, st>>>(block_sums, nb, total);
 }
 
 // Stable scatter of one 8-bit digit pass.  The tile's keys are first ranked
