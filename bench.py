@@ -615,26 +615,37 @@ def autograd_variant(gcp, torch, stream, steps=10, with_oracle=True):
     loss.backward()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ctx.profile(True)
-    ctx.profile_read()
     e0.record(stream)
+    h0 = time.perf_counter()
     for i in range(steps):
         for a in A:
             a.grad = None
         loss = autograd.sampled_loss(ctx, 1 + i, s, 0, A)
         loss.backward()
+    host_ms = (time.perf_counter() - h0) * 1e3 / steps  # host time to issue one iteration
     e1.record(stream)
     e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # the fused pass's own time, from the library's events, in a second loop
+    # (a first untimed one creates the events)
+    ctx.profile(True)
+    for rep in range(2):
+        ctx.profile_read()
+        for i in range(steps):
+            for a in A:
+                a.grad = None
+            loss = autograd.sampled_loss(ctx, 100 + i, s, 0, A)
+            loss.backward()
     kms, nl = ctx.profile_read()
     ctx.profile(False)
-    ms = e0.elapsed_time(e1) / steps
     ctx.close()
     # the fused pass's row traffic (5 rows of 64 B gathered and reduced per
     # sample) alone on an L2-resident buffer
     ceil = l2_ceiling(gcp, torch, stream, 5, 16, s, reps=5)
     fused_ms = kms / max(1, nl)
     out = {"workload": "dense 100x100x100x20x50, Gaussian, rank 16, 2^22 uniform samples",
-           "forward_backward_ms": ms, "samples_per_s": s / (ms / 1e3), "fused_kernel_ms": fused_ms,
+           "forward_backward_ms": ms, "samples_per_s": s / (ms / 1e3), "host_issue_ms": host_ms,
+           "fused_kernel_ms": fused_ms,
            "l2_rows_probe_ms": ceil["both"]["ms"], "l2_rows_frac": ceil["both"]["ms"] / fused_ms if nl else None}
     if cpu:
         out["cpu_oracle"] = cpu
@@ -694,6 +705,14 @@ def run_ours(args):
     adam = gcp.AdamParams(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, lower=0.0)
 
     def timed_loop(ctx, steps, warmup, profile):
+        if profile:  # one untimed pass creates the library's per-launch timing events
+            ctx.profile(True)
+            for i in range(steps):
+                ctx.step(50_000 + i, p, q, adam, i + 1)
+            ctx.profile_read()
+            ctx.profile(False)
+            ctx.set_factors(w["factors"])  # back to the starting state
+            ctx.reset_adam()
         for i in range(warmup):
             ctx.step(10_000 + i, p, q, adam, i + 1)
         ctx.sync()

@@ -185,6 +185,14 @@ int64_t gcp_num_params(const gcp_ctx *ctx);
 gcp_status gcp_set_factors(gcp_ctx *ctx, const float *A);
 /* Set one mode's factor matrix (host or device, I_mode x R FP32). */
 gcp_status gcp_set_factor(gcp_ctx *ctx, int32_t mode, const float *A_mode);
+/* Set every mode's factor matrix in one call: A_modes (host array of ndim
+ * pointers) points to the per-mode matrices (host or device, I_k x R FP32,
+ * row-major, each contiguous).  Asynchronous on the context's stream: the
+ * matrices must stay valid until the stream has consumed them; the pointer
+ * array itself is read before the call returns.  With BF16 storage the BF16
+ * copy is refreshed once.  The paper has no counterpart (the autograd
+ * binding stages its factor tensors with it). */
+gcp_status gcp_set_factor_list(gcp_ctx *ctx, const float *const *A_modes);
 /* Copy the FP32 master factors out (host or device, flat). Synchronises. */
 gcp_status gcp_get_factors(gcp_ctx *ctx, float *A_out);
 /* Zero the Adam moments. */
@@ -223,13 +231,14 @@ gcp_status gcp_grad(gcp_ctx *ctx, uint64_t iter, int64_t p, int64_t q, float *G_
 gcp_status gcp_grad_async(gcp_ctx *ctx, uint64_t iter, int64_t p, int64_t q, const float *dscale,
                           float *G_out, double *dloss_out);
 
-/* y[i] = dscale[0] * x[i] for i < n, on the context's stream.  dscale, x
- * and y are device pointers (y may equal x); nothing is allocated.  The
- * paper has no counterpart: the autograd binding computes the loss and the
- * gradient in one fused pass in the forward evaluation and applies the
- * incoming gradient in the backward evaluation with this call.
+/* y[i] = (float)dscale[0] * x[i] for i < n, on the context's stream.
+ * dscale (one FP64 value, as the FP64 loss's incoming gradient is), x and y
+ * are device pointers (y may equal x); nothing is allocated.  The paper has
+ * no counterpart: the autograd binding computes the loss and the gradient
+ * in one fused pass in the forward evaluation and applies the incoming
+ * gradient in the backward evaluation with this call.
  * GCP_ERR_ARG for a NULL pointer or n < 0. */
-gcp_status gcp_scale_async(gcp_ctx *ctx, const float *dscale, const float *x, float *y, int64_t n);
+gcp_status gcp_scale_async(gcp_ctx *ctx, const double *dscale, const float *x, float *y, int64_t n);
 
 /* One Adam step (Algorithm 1, one kernel over the flat parameter vector,
  * Sec. 3.1.3) with the gradient held by the context, t >= 1. */

@@ -79,6 +79,7 @@ SIGNATURES = {
     "gcp_num_params": (_i64, [_vp]),
     "gcp_set_factors": (_i32, [_vp, _vp]),
     "gcp_set_factor": (_i32, [_vp, _i32, _vp]),
+    "gcp_set_factor_list": (_i32, [_vp, _vp]),
     "gcp_get_factors": (_i32, [_vp, _vp]),
     "gcp_reset_adam": (_i32, [_vp]),
     "gcp_sample": (_i32, [_vp, _u64, _i64, _i64, _vp, _vp, _vp]),
@@ -200,6 +201,7 @@ class GcpContext:
         self.loss = loss
         self.dtype = dtype
         self.stream = stream
+        self._num_params = None
 
     # ------------------------------------------------------------ life
     def close(self):
@@ -221,7 +223,10 @@ class GcpContext:
 
     @property
     def num_params(self):
-        return int(load().gcp_num_params(self.handle))
+        """sum_k I_k * R, fixed for the context's life (asked once)."""
+        if self._num_params is None:
+            self._num_params = int(load().gcp_num_params(self.handle))
+        return self._num_params
 
     @property
     def nnz(self):
@@ -300,8 +305,9 @@ class GcpContext:
                self.handle)
 
     def scale_async(self, dscale, x, y):
-        """y = dscale[0] * x on the context's stream (device tensors)."""
-        _check_buf(dscale, 1, "float32", "dscale")
+        """y = dscale[0] * x on the context's stream (device tensors; dscale
+        holds one FP64 value)."""
+        _check_buf(dscale, 1, "float64", "dscale")
         _check_buf(x, 0, "float32", "x")
         _check_buf(y, x.numel(), "float32", "y")
         _check(load().gcp_scale_async(self.handle, _ptr(dscale), _ptr(x), _ptr(y), x.numel()), self.handle)

@@ -12,24 +12,28 @@ only moves pointers.
 """
 from __future__ import annotations
 
+import ctypes
+
 import torch
 
-from . import GcpContext, _check, _ptr, load
+from . import GcpContext, _check, load
 
 
 def _stage_factors(ctx: GcpContext, factors):
-    """Copy the factor tensors into the context (asynchronous, on its
-    stream); returns the FP32 contiguous tensors, which must stay alive
-    until the copies have run."""
+    """Copy the factor tensors into the context in one call (asynchronous,
+    on its stream); returns the FP32 contiguous tensors, which must stay
+    alive until the copies have run."""
     staged = []
+    ptrs = (ctypes.c_void_p * len(factors))()
     for k, a in enumerate(factors):
         t = a.detach()
         if t.dtype != torch.float32 or not t.is_contiguous():
             t = t.to(torch.float32).contiguous()
-        if tuple(t.shape) != (ctx.dims[k], ctx.rank):
+        if t.shape[0] != ctx.dims[k] or t.shape[1] != ctx.rank or t.dim() != 2:
             raise ValueError(f"factor {k} has shape {tuple(t.shape)}, expected {(ctx.dims[k], ctx.rank)}")
-        _check(load().gcp_set_factor(ctx.handle, k, _ptr(t)), ctx.handle)
+        ptrs[k] = t.data_ptr()
         staged.append(t)
+    _check(load().gcp_set_factor_list(ctx.handle, ptrs), ctx.handle)
     return staged
 
 
@@ -58,7 +62,7 @@ class GcpSampledLoss(torch.autograd.Function):
     @staticmethod
     def backward(fctx, grad_out):
         ctx: GcpContext = fctx.gcp
-        scale = grad_out.detach().to(torch.float32).reshape(1).contiguous()
+        scale = grad_out.detach().to(torch.float64).reshape(1).contiguous()  # no copy for an FP64 seed
         G = torch.empty_like(fctx.G)
         ctx.scale_async(scale, fctx.G, G)
         grads, o = [], 0

@@ -407,9 +407,10 @@ __global__ void k_check_dense(const float *X, int64_t n, int loss, int *status) 
     if (bad) atomicOr(status, bad);
 }
 
-// y = s[0] * x elementwise (x and y may be the same array).
-__global__ void k_scale(const float *s, const float *x, float *y, int64_t n) {
-    const float a = __ldg(s);
+// y = s[0] * x elementwise (x and y may be the same array); s is FP64,
+// rounded once to FP32.
+__global__ void k_scale(const double *s, const float *x, float *y, int64_t n) {
+    const float a = (float)__ldg(s);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = a * x[i];
 }
@@ -664,6 +665,17 @@ gcp_status gcp_set_factor(gcp_ctx *c, int32_t mode, const float *A_mode) {
     return refresh_bf16(c);
 }
 
+gcp_status gcp_set_factor_list(gcp_ctx *c, const float *const *A_modes) {
+    if (!c || !A_modes) return fail(c, GCP_ERR_ARG, "NULL argument");
+    for (int k = 0; k < c->d; ++k)
+        if (!A_modes[k]) return fail(c, GCP_ERR_ARG, "NULL factor pointer");
+    DeviceGuard g(c->device);
+    for (int k = 0; k < c->d; ++k)
+        GCP_CUDA(c, cudaMemcpy2DAsync(c->A + c->rowoff[k] * c->Rp, (size_t)c->Rp * 4, A_modes[k], (size_t)c->R * 4,
+                                      (size_t)c->R * 4, (size_t)c->dims[k], cudaMemcpyDefault, c->st));
+    return refresh_bf16(c);
+}
+
 gcp_status gcp_get_factors(gcp_ctx *c, float *A_out) {
     if (!c || !A_out) return fail(c, GCP_ERR_ARG, "NULL argument");
     DeviceGuard g(c->device);
@@ -734,7 +746,7 @@ gcp_status gcp_grad_async(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, const
     return GCP_OK;
 }
 
-gcp_status gcp_scale_async(gcp_ctx *c, const float *dscale, const float *x, float *y, int64_t n) {
+gcp_status gcp_scale_async(gcp_ctx *c, const double *dscale, const float *x, float *y, int64_t n) {
     if (!c) return fail(c, GCP_ERR_ARG, "NULL context");
     if (!dscale || !x || !y || n < 0) return fail(c, GCP_ERR_ARG, "NULL array or negative length");
     if (n == 0) return GCP_OK;

@@ -12,7 +12,9 @@
 //                   factor gathers;
 //   GCP_PROBE_BOTH: per op, `rows_per_op` rows read, then `rows_per_op`
 //                   other rows added -- one sample's model traffic.
-// Rows are drawn by a splitmix64 hash of the op index, uniformly.
+// Rows are drawn by a splitmix64 hash of the op index, uniformly.  The lanes
+// of a group cover a row as the fused pass's do: one 16-byte quad per lane
+// for rows of up to 32 floats, two (columns 4g.. and Rp/2 + 4g..) above.
 #include "../../include/gcp.h"
 #include "gcp_device.cuh"
 #include "gcp_internal.h"
@@ -23,10 +25,10 @@ namespace {
 
 constexpr int kProbeThreads = 256;
 
-template <int KIND>
+template <int KIND, int NQ>
 __global__ void __launch_bounds__(kProbeThreads) k_probe(float *__restrict__ buf, int64_t rows, int log2L,
                                                          int rows_per_op, int64_t ops, float *sink) {
-    const int L = 1 << log2L, Rp = 4 * L;
+    const int L = 1 << log2L, Rp = 4 * NQ * L;
     const int lane = threadIdx.x & 31, glane = lane & (L - 1);
     const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> log2L;
     const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> log2L;
@@ -36,8 +38,12 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(float *__restrict__ buf
         if (KIND != 0) {
             for (int k = 0; k < rows_per_op; ++k) {
                 const int64_t r = (int64_t)__umul64hi(h, (uint64_t)rows);
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(buf + r * Rp + 4 * glane));
-                acc += v.x + v.y + v.z + v.w;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const float4 v =
+                        __ldg(reinterpret_cast<const float4 *>(buf + r * Rp + q * (Rp >> 1) + 4 * glane));
+                    acc += v.x + v.y + v.z + v.w;
+                }
                 h = mix64(h);
             }
         }
@@ -45,7 +51,8 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(float *__restrict__ buf
             const float y = 1e-30f * (float)(op & 7);
             for (int k = 0; k < rows_per_op; ++k) {
                 const int64_t r = (int64_t)__umul64hi(h, (uint64_t)rows);
-                red_add_v4(buf + r * Rp + 4 * glane, y + acc, y, y, y);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) red_add_v4(buf + r * Rp + q * (Rp >> 1) + 4 * glane, y + acc, y, y, y);
                 h = mix64(h);
             }
         }
@@ -70,7 +77,8 @@ extern "C" gcp_status gcp_probe_l2(int32_t kind, int32_t row_floats, int32_t row
         gcpk_set_noctx_error("gcp_probe_l2: rows_per_op in 1..8, rows >= 1, ops >= 0, 16-byte aligned buffer");
         return GCP_ERR_ARG;
     }
-    const int L = row_floats / 4;
+    const int nq = row_floats > 32 ? 2 : 1;  // quads per lane, as in the fused pass
+    const int L = row_floats / (4 * nq);
     int log2L = 0;
     while ((1 << log2L) < L) ++log2L;
     int dev = 0, sms = 0;
@@ -83,12 +91,16 @@ extern "C" gcp_status gcp_probe_l2(int32_t kind, int32_t row_floats, int32_t row
     if (blocks < 1) return GCP_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // rows x row_floats floats; the load probe's sink is the buffer's first float
+#define GCP_PROBE_LAUNCH(K)                                                                             \
+    (nq == 2 ? k_probe<K, 2><<<(int)blocks, kProbeThreads, 0, st>>>(buf, rows, log2L, rows_per_op, ops, buf) \
+             : k_probe<K, 1><<<(int)blocks, kProbeThreads, 0, st>>>(buf, rows, log2L, rows_per_op, ops, buf))
     if (kind == GCP_PROBE_RED)
-        k_probe<0><<<(int)blocks, kProbeThreads, 0, st>>>(buf, rows, log2L, rows_per_op, ops, buf);
+        GCP_PROBE_LAUNCH(0);
     else if (kind == GCP_PROBE_LOAD)
-        k_probe<1><<<(int)blocks, kProbeThreads, 0, st>>>(buf, rows, log2L, rows_per_op, ops, buf);
+        GCP_PROBE_LAUNCH(1);
     else
-        k_probe<2><<<(int)blocks, kProbeThreads, 0, st>>>(buf, rows, log2L, rows_per_op, ops, buf);
+        GCP_PROBE_LAUNCH(2);
+#undef GCP_PROBE_LAUNCH
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         gcpk_set_noctx_error(cudaGetErrorString(e));

@@ -95,6 +95,14 @@ def test_host_argument_checks_need_no_gpu(lib_path):
     assert h.value is None
 
 
+def test_factor_list_and_scale_reject_null_arguments_on_the_host(lib_path):
+    import paper_2605_20353_gb300 as gcp
+
+    lib = gcp.load()
+    assert lib.gcp_set_factor_list(None, None) == 1
+    assert lib.gcp_scale_async(None, None, None, None, 4) == 1
+
+
 def test_l2_probe_rejects_bad_sizes_on_the_host(lib_path):
     """The measurement probe checks its sizes before any CUDA call."""
     import paper_2605_20353_gb300 as gcp

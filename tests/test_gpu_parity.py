@@ -624,3 +624,11 @@ def test_l2_probe_performs_every_row_operation(env):
     gcp.gcp_probe_l2("both", buf, 16, 3, ops)
     torch.cuda.synchronize()
     assert bool(torch.isfinite(buf).all()) and float(buf.double().sum()) > total
+    # rows wider than 32 floats: two quads per lane, as in the fused pass
+    wide = torch.zeros(2048 * 64, dtype=torch.float32, device="cuda")
+    gcp.gcp_probe_l2("red", wide, 64, 3, ops)
+    torch.cuda.synchronize()
+    expect = 3 * 64 * 1e-30 * float(k.sum())
+    total = float(wide.double().sum())
+    assert abs(total - expect) <= 1e-4 * expect, (total, expect)
+    assert float(wide.view(2048, 64).double().sum(0).min()) > 0.0  # every column was reached
