@@ -393,12 +393,13 @@ __device__ __forceinline__ void fold_quad(const ClientAux &a, int hs, int col, f
 // The epilogue of one local step of every client, one launch over a chunk
 // list built at batch creation.  A chunk {client, -1} finishes that client's
 // loss; a chunk {client, q} takes the client's parameter quads q ..
-// q + kPostQuads - 1, two per thread with all gradient loads issued first:
+// q + kPostQuads - 1, kPostUnroll per thread with all gradient loads issued first:
 // the gradient quad plus, for a hot row, its replica quads (replicas
 // cleared), then Algorithm 1 on the four entries.  G itself is cleared at
 // the start of the next step, just before the fused pass, so that its lines
 // are still in L2 when the reductions arrive.
-constexpr int kPostQuads = 2 * kThreads;
+constexpr int kPostUnroll = 2;
+constexpr int kPostQuads = kPostUnroll * kThreads;
 
 __global__ void __launch_bounds__(kThreads, 4) k_batch_post(const ClientAux *__restrict__ aux,
                                                             const int2 *__restrict__ chunks,
@@ -414,12 +415,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_post(const ClientAux *__r
                        (float)adam[4], (float)adam[5], (float)adam[6]};
     const int log2Rp = __ffs(a.Rp) - 1;  // Rp is a power of two and a multiple of 4
     const int64_t nq = a.nparam >> 2;
-    const int64_t q[2] = {(int64_t)ch.y + threadIdx.x, (int64_t)ch.y + threadIdx.x + kThreads};
-    const float4 *G4 = reinterpret_cast<const float4 *>(a.G);
-    float4 g4[2];
-    int col[2], hs[2];
+    int64_t q[kPostUnroll];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < kPostUnroll; ++u) q[u] = (int64_t)ch.y + threadIdx.x + u * kThreads;
+    const float4 *G4 = reinterpret_cast<const float4 *>(a.G);
+    float4 g4[kPostUnroll];
+    int col[kPostUnroll], hs[kPostUnroll];
+#pragma unroll
+    for (int u = 0; u < kPostUnroll; ++u) {
         col[u] = (int)((q[u] << 2) & (a.Rp - 1));
         hs[u] = -1;
         if (q[u] < nq) {
@@ -428,18 +431,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_post(const ClientAux *__r
         }
     }
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+    for (int u = 0; u < kPostUnroll; ++u)
         if (hs[u] >= 0) fold_quad(a, hs[u], col[u], g4[u]);
-    float4 b4[2], c4[2], x4[2];
+    float4 b4[kPostUnroll], c4[kPostUnroll], x4[kPostUnroll];
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+    for (int u = 0; u < kPostUnroll; ++u)
         if (q[u] < nq && col[u] < a.R) {
             b4[u] = reinterpret_cast<const float4 *>(a.B)[q[u]];
             c4[u] = reinterpret_cast<const float4 *>(a.C)[q[u]];
             x4[u] = reinterpret_cast<const float4 *>(a.A)[q[u]];
         }
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+    for (int u = 0; u < kPostUnroll; ++u)
         if (q[u] < nq && col[u] < a.R) adam_quad(a, q[u], col[u], g4[u], b4[u], c4[u], x4[u], k);
 }
 

@@ -99,3 +99,34 @@ def test_autograd_loss_only_and_partial_grads(env):
     for k in (0, 2):
         assert rel_err(A[k].grad.cpu().numpy(), 2.5 * Go[k]) <= TOL, k
     ctx.close()
+
+
+def bf16_round(a):
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16).astype(np.uint32).view(np.float32)
+
+
+def test_autograd_bf16_padded_rank_and_fp64_noncontiguous_factors(env):
+    """BF16 factor storage with rank 6 (rows padded to 8 columns): the
+    factors are staged in one call into the padded layout and their BF16
+    copy refreshed once; FP64 and transposed (non-contiguous) factor tensors
+    are converted first.  Loss and gradients match the oracle run on the
+    BF16-rounded factors."""
+    gcp, torch, ag = env
+    dims = [35, 25, 15]
+    coords, vals = synth.uniform_sparse(dims, 1200, 61, lam=2.0)
+    fac = synth.factors_uniform(dims, 6, 62, lo=0.1, hi=1.0)
+    ctx = gcp.gcp_create(dims, coords, vals, 6, "poisson", dtype="bf16", seed=63)
+    A = [torch.tensor(fac[0], device="cuda", dtype=torch.float64, requires_grad=True),
+         torch.tensor(fac[1].T.copy(), device="cuda").t().detach().requires_grad_(True),  # non-contiguous view
+         torch.tensor(fac[2], device="cuda", requires_grad=True)]
+    assert not A[1].is_contiguous()
+    loss = ag.sampled_loss(ctx, 2, 800, 900, A)
+    loss.backward()
+    idx, x, w, _ = oracle.stratified_samples(63, 2, 800, 900, dims, coords, vals)
+    Lo, Go = oracle.sampled_loss_grad(dims, [bf16_round(a) for a in fac], "poisson", idx, x, w)
+    assert abs(loss.item() - Lo) <= TOL * abs(Lo)
+    for k in range(3):
+        assert A[k].grad.shape == (dims[k], 6)
+        assert rel_err(A[k].grad.double().cpu().numpy(), Go[k]) <= TOL, k
+    ctx.close()
