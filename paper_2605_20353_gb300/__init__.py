@@ -239,6 +239,10 @@ class GcpContext:
         import torch
 
         if isinstance(factors, (list, tuple)):
+            if len(factors) != len(self.dims):
+                raise ValueError(f"expected {len(self.dims)} factor matrices, got {len(factors)}")
+            staged = []
+            ptrs = (ctypes.c_void_p * len(factors))()
             for k, a in enumerate(factors):
                 if isinstance(a, np.ndarray):
                     a = np.ascontiguousarray(a, dtype=np.float32)
@@ -246,10 +250,10 @@ class GcpContext:
                     a = a.detach().to(torch.float32).contiguous()
                 if tuple(a.shape) != (self.dims[k], self.rank):
                     raise ValueError(f"factor {k} has shape {tuple(a.shape)}, expected {(self.dims[k], self.rank)}")
-                _check(load().gcp_set_factor(self.handle, k, _ptr(a)), self.handle)
-                if not isinstance(a, np.ndarray):
-                    self._keep = a
-            self.sync()
+                ptrs[k] = _ptr(a)
+                staged.append(a)
+            _check(load().gcp_set_factor_list(self.handle, ptrs), self.handle)
+            self.sync()  # the copies have run: the staged arrays may go
             return
         a = factors
         if isinstance(a, np.ndarray):
