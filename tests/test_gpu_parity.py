@@ -99,6 +99,22 @@ def test_sample_bit_exact_small(env, t):
     ctx.close()
 
 
+def test_sample_bit_exact_over_2_24_counters(env):
+    """2^23 nonzero + 2^23 zero draws (with about 2.9e5 rejected zero
+    candidates redrawn) on the 50x40x30 tensor: every index equals the
+    oracle's, so the device Philox and range map agree with the host's over
+    2^24 counters."""
+    gcp, torch = env
+    w = synth.workload_small_gaussian()
+    ctx = gcp.gcp_create(w["dims"], w["coords"], w["vals"], 4, "gaussian", seed=0x5EED)
+    p = q = 1 << 23
+    idx, _, _ = ctx.sample(12345, p, q)
+    ido, _, _, att = oracle.stratified_samples(0x5EED, 12345, p, q, w["dims"], w["coords"], w["vals"])
+    assert att > q  # some zero candidates were nonzeros and were redrawn
+    assert np.array_equal(idx.cpu().numpy(), ido)
+    ctx.close()
+
+
 def test_sample_bit_exact_zipf_4way(env):
     gcp, torch = env
     w = synth.workload_zipf_count(scale=0.01)
