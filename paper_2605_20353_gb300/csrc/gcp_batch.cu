@@ -85,7 +85,7 @@ __device__ __forceinline__ int client_of(const int *__restrict__ tile_start, int
 // tensor, model, gradient and weights; the iteration number is step[0].
 // Per tile, the FP32 loss sums (nonzero, zero) go to tile_loss[tile].
 template <int D, typename TF, int COLS>
-__global__ void __launch_bounds__(kThreads) k_batch_fused(const int4 *__restrict__ specs,
+__global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) k_batch_fused(const int4 *__restrict__ specs,
                                                          const int *__restrict__ tile_start, int nclients,
                                                          int total_tiles, int log2L, int Rp,
                                                          const uint64_t *__restrict__ step, float2 *tile_loss) {
