@@ -57,11 +57,21 @@ def algorithmic_bytes_per_sample(d, R, nnz, M, elt_bytes):
     return 0.5 * (4 * (d + 1) + rows) + 0.5 * (32 * attempts + rows)
 
 
+# the fused pass's part of gcp_kernels.cu ends where the replica fold begins
+FUSED_SECTION_END = b"// G(hot row) += sum over replicas"
+
+
 def kernel_source_hash():
+    """Hash of the fused kernel's source: the device header and the part of
+    gcp_kernels.cu up to the replica fold (the whole file if that marker
+    moved), so that edits to other kernels keep the captured counters."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+            text = fh.read()
+        if f.endswith("gcp_kernels.cu") and FUSED_SECTION_END in text:
+            text = text[:text.index(FUSED_SECTION_END)]
+        h.update(text)
     return h.hexdigest()[:16]
 
 
