@@ -240,6 +240,14 @@ gcp_status gcp_grad_async(gcp_ctx *ctx, uint64_t iter, int64_t p, int64_t q, con
  * GCP_ERR_ARG for a NULL pointer or n < 0. */
 gcp_status gcp_scale_async(gcp_ctx *ctx, const double *dscale, const float *x, float *y, int64_t n);
 
+/* Frobenius norm of the gradient the context holds (after gcp_grad or
+ * gcp_grad_async; zero after gcp_step, which clears it), summed in FP64 on
+ * the device in a fixed order, so that repeated calls agree bit for bit;
+ * *norm_out (host) receives it.  GCP_ERR_NONFINITE if the gradient holds a
+ * NaN or an infinity.  Synchronises the context's stream.  The paper has no
+ * counterpart: it is the FP64 check kept beside the FP32 / BF16 path. */
+gcp_status gcp_grad_norm(gcp_ctx *ctx, double *norm_out);
+
 /* One Adam step (Algorithm 1, one kernel over the flat parameter vector,
  * Sec. 3.1.3) with the gradient held by the context, t >= 1. */
 gcp_status gcp_adam_step(gcp_ctx *ctx, const gcp_adam_params *prm, int64_t t);

@@ -88,6 +88,7 @@ SIGNATURES = {
     "gcp_grad": (_i32, [_vp, _u64, _i64, _i64, _vp, _vp]),
     "gcp_grad_async": (_i32, [_vp, _u64, _i64, _i64, _vp, _vp, _vp]),
     "gcp_scale_async": (_i32, [_vp, _vp, _vp, _vp, _i64]),
+    "gcp_grad_norm": (_i32, [_vp, ctypes.POINTER(_f64)]),
     "gcp_adam_step": (_i32, [_vp, ctypes.POINTER(gcp_adam_params), _i64]),
     "gcp_step": (_i32, [_vp, _u64, _i64, _i64, ctypes.POINTER(gcp_adam_params), _i64, _vp]),
     "gcp_sync": (_i32, [_vp]),
@@ -319,6 +320,12 @@ class GcpContext:
     def loss_async(self, iter, p, q, dloss):
         _check_buf(dloss, 1, "float64", "dloss")
         _check(load().gcp_loss_async(self.handle, iter, p, q, _ptr(dloss)), self.handle)
+
+    def grad_norm(self):
+        """||G||_F of the gradient the context holds, in FP64 (synchronises)."""
+        v = ctypes.c_double(0.0)
+        _check(load().gcp_grad_norm(self.handle, ctypes.byref(v)), self.handle)
+        return v.value
 
     def adam_step(self, prm: AdamParams, t: int):
         c = prm.c()

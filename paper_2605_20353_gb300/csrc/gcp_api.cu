@@ -415,6 +415,34 @@ __global__ void k_scale(const double *s, const float *x, float *y, int64_t n) {
         y[i] = a * x[i];
 }
 
+// Sum of squares of x[0..n) in FP64: block b adds its grid-stride elements
+// in index order per thread, then a fixed tree; partial[b] holds the result.
+__global__ void k_sumsq_blocks(const float *__restrict__ x, int64_t n, double *partial) {
+    __shared__ double sh[256];
+    double t = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)x[i];
+        t += v * v;
+    }
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// out[0] = sqrt(sum of the block partials), summed in block order; a
+// non-finite result sets the status word.
+__global__ void k_sumsq_finish(const double *__restrict__ partial, int nblocks, double *out, int *status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partial[b];
+    out[0] = sqrt(t);
+    if (!isfinite(t)) atomicOr(status, 1 << GCP_ERR_NONFINITE);
+}
+
 gcp_status copy_grad_out(gcp_ctx *c, float *G_out) {
     if (!G_out) return GCP_OK;
     GCP_CUDA(c, cudaMemcpy2DAsync(G_out, (size_t)c->R * 4, c->G, (size_t)c->Rp * 4, (size_t)c->R * 4,
@@ -775,6 +803,22 @@ gcp_status gcp_step(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, const gcp_a
     if (dloss_out)
         GCP_CUDA(c, cudaMemcpyAsync(dloss_out, c->dloss, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     return GCP_OK;
+}
+
+gcp_status gcp_grad_norm(gcp_ctx *c, double *norm_out) {
+    if (!c || !norm_out) return fail(c, GCP_ERR_ARG, "NULL argument");
+    DeviceGuard g(c->device);
+    const int64_t n = (int64_t)c->total_rows * c->Rp;  // padding columns hold zeros
+    const int64_t want = (n + 255) / 256;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(want, 4 * (int64_t)c->max_blocks));
+    // the loss partials are free once the gradient's loss is finished (stream order)
+    k_sumsq_blocks<<<nb, 256, 0, c->st>>>(c->G, n, c->partials);
+    k_sumsq_finish<<<1, 32, 0, c->st>>>(c->partials, nb, c->dloss + 2, c->status);
+    GCP_CUDA(c, cudaGetLastError());
+    GCP_CUDA(c, cudaMemcpyAsync(c->h_loss + 2, c->dloss + 2, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    const gcp_status s = collect(c);  // synchronises
+    *norm_out = c->h_loss[2];
+    return s;
 }
 
 gcp_status gcp_sync(gcp_ctx *c) {

@@ -128,7 +128,7 @@ struct gcp_ctx {
     float *B = nullptr, *C = nullptr;  // Adam moments
     double *partials = nullptr;   // per-block reduction partials
     int max_blocks = 0;
-    double *dloss = nullptr;      // [0] loss, [1] zero attempts
+    double *dloss = nullptr;      // [0] loss, [1] zero attempts, [2] gradient norm
     int *status = nullptr;        // device status word
     int *h_status = nullptr;      // pinned mirror
     double *h_loss = nullptr;     // pinned mirror of dloss

@@ -101,6 +101,7 @@ def test_factor_list_and_scale_reject_null_arguments_on_the_host(lib_path):
     lib = gcp.load()
     assert lib.gcp_set_factor_list(None, None) == 1
     assert lib.gcp_scale_async(None, None, None, None, 4) == 1
+    assert lib.gcp_grad_norm(None, None) == 1
 
 
 def test_l2_probe_rejects_bad_sizes_on_the_host(lib_path):

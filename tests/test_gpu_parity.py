@@ -210,6 +210,38 @@ def test_grad_dense_uniform(env):
     ctx.close()
 
 
+def test_gradient_norm_in_fp64(env):
+    """gcp_grad_norm: the FP64 Frobenius norm of the context's gradient
+    equals the oracle gradient's norm, repeats bit for bit, and is zero once
+    gcp_step has cleared the gradient."""
+    gcp, torch = env
+    w = synth.workload_small_gaussian()
+    ctx = gcp.gcp_create(w["dims"], w["coords"], w["vals"], 4, "gaussian", seed=3001)
+    ctx.set_factors(w["factors"])
+    ctx.grad(2, w["p"], w["q"])
+    n1, n2 = ctx.grad_norm(), ctx.grad_norm()
+    idx, x, wt, _ = oracle.stratified_samples(3001, 2, w["p"], w["q"], w["dims"], w["coords"], w["vals"])
+    _, Go = oracle.sampled_loss_grad(w["dims"], w["factors"], "gaussian", idx, x, wt)
+    ref = float(np.linalg.norm(np.concatenate([g.ravel() for g in Go])))
+    assert abs(n1 - ref) <= TOL_FP32 * ref, (n1, ref)
+    assert n1 == n2
+    ctx.step(3, w["p"], w["q"], gcp.AdamParams(lr=1e-3), 1)
+    assert ctx.grad_norm() == 0.0
+    # a NaN factor entry: the loss and the norm check both report it, and the
+    # context stays usable once the factors are finite again
+    bad = [a.copy() for a in w["factors"]]
+    bad[0][0, 0] = np.nan
+    ctx.set_factors(bad)
+    with pytest.raises(gcp.GcpError):
+        ctx.grad(4, w["p"], w["q"])
+    with pytest.raises(gcp.GcpError):
+        ctx.grad_norm()
+    ctx.set_factors(w["factors"])
+    ctx.grad(2, w["p"], w["q"])
+    assert abs(ctx.grad_norm() - n1) <= TOL_FP32 * n1  # same samples; atomic order may differ
+    ctx.close()
+
+
 def test_loss_only_call_matches_grad_call(env):
     gcp, torch = env
     w = synth.workload_small_gaussian()
