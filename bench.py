@@ -641,6 +641,19 @@ def autograd_variant(gcp, torch, stream, steps=10, with_oracle=True):
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    # the other split: loss-only forward, MTTKRP adjoint in the backward
+    for i in range(2):
+        loss = autograd.sampled_loss(ctx, 50 + i, s, 0, A, grad_in_forward=False)
+        loss.backward()
+    e0.record(stream)
+    for i in range(steps):
+        for a in A:
+            a.grad = None
+        loss = autograd.sampled_loss(ctx, 60 + i, s, 0, A, grad_in_forward=False)
+        loss.backward()
+    e1.record(stream)
+    e1.synchronize()
+    ms_adjoint = e0.elapsed_time(e1) / steps
     # the fused pass's own time, from the library's events, in a second loop
     # (a first untimed one creates the events)
     ctx.profile(True)
@@ -660,6 +673,7 @@ def autograd_variant(gcp, torch, stream, steps=10, with_oracle=True):
     fused_ms = kms / max(1, nl)
     out = {"workload": "dense 100x100x100x20x50, Gaussian, rank 16, 2^22 uniform samples",
            "forward_backward_ms": ms, "samples_per_s": s / (ms / 1e3), "host_issue_ms": host_ms,
+           "forward_backward_ms_adjoint_in_backward": ms_adjoint,
            "fused_kernel_ms": fused_ms,
            "l2_rows_probe_ms": ceil["both"]["ms"], "l2_rows_frac": ceil["both"]["ms"] / fused_ms if nl else None}
     if cpu:

@@ -7,8 +7,11 @@ gradient (Eq. gcp-gradient) with a unit seed, so each sample is drawn and
 its Khatri-Rao rows gathered once; nothing per sample is stored, only the
 gradient itself (sum_k I_k R floats).  Backward multiplies that gradient by
 the incoming one on the device.  Without factor gradients the forward pass
-computes the loss alone.  All arithmetic runs in libgcp.so; this module
-only moves pointers.
+computes the loss alone.  The other split, GcpSampledLossAdjoint
+(grad_in_forward=False), computes the loss alone in the forward and runs the
+fused MTTKRP adjoint kernel in the backward, seeded with the incoming
+gradient.  All arithmetic runs in libgcp.so; this module only moves
+pointers.
 """
 from __future__ import annotations
 
@@ -74,5 +77,43 @@ class GcpSampledLoss(torch.autograd.Function):
         return (None, None, None, None, *grads)
 
 
-def sampled_loss(ctx: GcpContext, iteration: int, p: int, q: int, factors):
-    return GcpSampledLoss.apply(ctx, iteration, p, q, *factors)
+class GcpSampledLossAdjoint(torch.autograd.Function):
+    """Same loss, other split of the work: the forward computes the sampled
+    loss alone; the backward runs the fused MTTKRP adjoint kernel once more
+    over the same sample set (same iteration, so the same samples), seeded
+    with the incoming gradient, recomputing the Khatri-Rao rows.  It costs a
+    second sampling pass, and suits graphs whose backward may not run."""
+
+    @staticmethod
+    def forward(fctx, ctx: GcpContext, iteration: int, p: int, q: int, *factors):
+        staged = _stage_factors(ctx, factors)
+        loss = torch.empty(1, dtype=torch.float64, device=factors[0].device)
+        ctx.loss_async(iteration, p, q, loss)
+        fctx.gcp, fctx.args, fctx.staged = ctx, (iteration, p, q), staged
+        fctx.save_for_backward(*[f.detach() for f in factors])
+        return loss.reshape(())
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        ctx: GcpContext = fctx.gcp
+        factors = fctx.saved_tensors
+        staged = _stage_factors(ctx, factors)  # the factors as of the forward pass
+        seed = grad_out.detach().to(torch.float32).reshape(1).contiguous()
+        G = torch.empty(ctx.num_params, dtype=torch.float32, device=seed.device)
+        ctx.grad_async(*fctx.args, dscale=seed, G_out=G)
+        grads, o = [], 0
+        for k, I in enumerate(ctx.dims):
+            g = G[o:o + I * ctx.rank].view(I, ctx.rank)
+            grads.append(g if fctx.needs_input_grad[4 + k] else None)
+            o += I * ctx.rank
+        fctx.staged = fctx.staged + staged + [seed]  # alive until the stream has consumed them
+        return (None, None, None, None, *grads)
+
+
+def sampled_loss(ctx: GcpContext, iteration: int, p: int, q: int, factors, grad_in_forward: bool = True):
+    """The sampled GCP loss of iteration `iteration` as a differentiable
+    0-dim FP64 tensor.  grad_in_forward=True (default) forms the gradient in
+    the forward's fused pass and only scales it in the backward; False runs
+    the MTTKRP adjoint in the backward instead (GcpSampledLossAdjoint)."""
+    fn = GcpSampledLoss if grad_in_forward else GcpSampledLossAdjoint
+    return fn.apply(ctx, iteration, p, q, *factors)

@@ -130,3 +130,27 @@ def test_autograd_bf16_padded_rank_and_fp64_noncontiguous_factors(env):
         assert A[k].grad.shape == (dims[k], 6)
         assert rel_err(A[k].grad.double().cpu().numpy(), Go[k]) <= TOL, k
     ctx.close()
+
+
+@pytest.mark.parametrize("scale", [1.0, -3.0])
+def test_autograd_adjoint_in_backward(env, scale):
+    """grad_in_forward=False: the forward computes the loss alone and the
+    backward runs the fused MTTKRP adjoint over the same samples, seeded with
+    the incoming gradient; loss and gradients match the oracle, also when
+    the context's factors were changed between forward and backward."""
+    gcp, torch, ag = env
+    dims = [40, 30, 20]
+    coords, vals = synth.uniform_sparse(dims, 1500, 71, lam=2.0)
+    fac = synth.factors_uniform(dims, 8, 72, lo=0.1, hi=1.0)
+    other = synth.factors_uniform(dims, 8, 73, lo=0.1, hi=1.0)
+    ctx = gcp.gcp_create(dims, coords, vals, 8, "poisson", seed=74)
+    A = [torch.tensor(a, device="cuda", requires_grad=True) for a in fac]
+    loss = ag.sampled_loss(ctx, 5, 900, 1100, A, grad_in_forward=False)
+    ctx.set_factors(other)  # the backward must use the forward's factors
+    (scale * loss).backward()
+    idx, x, w, _ = oracle.stratified_samples(74, 5, 900, 1100, dims, coords, vals)
+    Lo, Go = oracle.sampled_loss_grad(dims, fac, "poisson", idx, x, w)
+    assert abs(loss.item() - Lo) <= TOL * abs(Lo)
+    for n, (a, g) in enumerate(zip(A, Go)):
+        assert rel_err(a.grad.cpu().numpy(), scale * g) <= TOL, n
+    ctx.close()
