@@ -35,16 +35,20 @@ constexpr int kScanBlock = 2048;   // elements per block of the multi-block scan
 constexpr int kAhead = 4;          // carry vectors fetched ahead in the reduction of levels 2+
 
 // --------------------------------------------------------------- radix sort
+// Digits of NB = 256 (8 bits) or 1024 (10 bits) values: keys of up to 10
+// bits sort in one pass, longer ones in 8-bit passes.  hist[d * ntiles + t]
+// counts digit d in tile t.
+template <int NB>
 __global__ void k_radix_hist(const int32_t *__restrict__ keys, int key_stride, int64_t n, int shift,
                              int32_t *__restrict__ hist, int ntiles) {
-    __shared__ int h[256];
-    h[threadIdx.x] = 0;
+    __shared__ int h[NB];
+    for (int d = threadIdx.x; d < NB; d += kT) h[d] = 0;
     __syncthreads();
     const int64_t first = (int64_t)blockIdx.x * kTile;
     for (int i = threadIdx.x; i < kTile && first + i < n; i += kT)
-        atomicAdd(&h[(keys[(first + i) * key_stride] >> shift) & 255], 1);
+        atomicAdd(&h[(keys[(first + i) * key_stride] >> shift) & (NB - 1)], 1);
     __syncthreads();
-    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    for (int d = threadIdx.x; d < NB; d += kT) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
 }
 
 // Scan phases: each block of kScanBlock elements scans itself in place and
@@ -132,29 +136,42 @@ void scan_two_part(const int32_t *in, int32_t *a, int64_t n, bool flags, int32_t
     if (nb > 1) k_scan_top<<<1, kT, 0, st>>>(block_sums, nb, total);
 }
 
-// Stable scatter of one 8-bit digit pass.  The tile's keys are first ranked
-// into shared memory in index order (rounds of kT keys, warps in order,
-// lanes in order), which leaves the tile sorted by digit; the sorted tile is
-// then written out in order, so consecutive threads store consecutive
-// positions of a digit's run and the global writes are coalesced.
+// Stable scatter of one digit pass (NB digit values).  The tile's keys are
+// first ranked into shared memory in index order (rounds of kT keys, warps
+// in order, lanes in order), which leaves the tile sorted by digit; the
+// sorted tile is then written out in order, so consecutive threads store
+// consecutive positions of a digit's run and the global writes are
+// coalesced.  Thread t looks after digits t, t + kT, ... (NB / kT of them).
+// Shared memory (dynamic): keys and values of the tile, then per digit the
+// next local position, the global shift and one count per warp.
 constexpr int kKeysPerThread = kTile / kT;
 
+template <int NB>
+constexpr size_t scatter_smem_bytes() {
+    return (size_t)(2 * kTile + 2 * NB + (kT / 32) * NB + kT / 32) * sizeof(int32_t);
+}
+
+template <int NB>
 __global__ void __launch_bounds__(kT) k_radix_scatter(const int32_t *__restrict__ keys, int key_stride,
                                                       const int32_t *__restrict__ vals, int64_t n, int shift,
                                                       const int32_t *__restrict__ offsets,
                                                       const int32_t *__restrict__ offset_blocks, int ntiles,
                                                       int32_t *__restrict__ keys_out, int32_t *__restrict__ vals_out) {
-    __shared__ int32_t s_key[kTile], s_val[kTile];
-    __shared__ int running[256];  // next local position of each digit
-    __shared__ int gshift[256];   // global position - local position, per digit
-    __shared__ int wcount[kT / 32][256];
-    __shared__ int wsum[kT / 32];
+    constexpr int DPT = NB / kT;  // digits per thread
+    extern __shared__ __align__(16) int32_t smem[];
+    int32_t *s_key = smem, *s_val = smem + kTile;
+    int *running = smem + 2 * kTile;          // [NB]
+    int *gshift = running + NB;               // [NB]
+    int *wcount = gshift + NB;                // [kT / 32][NB]
+    int *wsum = wcount + (kT / 32) * NB;      // [kT / 32]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t first = (int64_t)blockIdx.x * kTile;
     const int tile_n = n - first < kTile ? (int)(n - first) : kTile;
     int32_t key[kKeysPerThread], val[kKeysPerThread];
-    running[threadIdx.x] = 0;
-    for (int w = 0; w < kT / 32; ++w) wcount[w][threadIdx.x] = 0;
+    for (int d = threadIdx.x; d < NB; d += kT) {
+        running[d] = 0;
+        for (int w = 0; w < kT / 32; ++w) wcount[w * NB + d] = 0;
+    }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kKeysPerThread; ++r) {
@@ -164,13 +181,19 @@ __global__ void __launch_bounds__(kT) k_radix_scatter(const int32_t *__restrict_
         if (i < tile_n) {
             key[r] = keys[(first + i) * key_stride];
             val[r] = vals ? vals[first + i] : (int32_t)(first + i);
-            atomicAdd(&running[(key[r] >> shift) & 255], 1);  // the tile's digit counts
+            atomicAdd(&running[(key[r] >> shift) & (NB - 1)], 1);  // the tile's digit counts
         }
     }
     __syncthreads();
-    // exclusive scan of the 256 digit counts (thread = digit)
-    const int cnt = running[threadIdx.x];
-    int incl = cnt;
+    // exclusive scan of the NB digit counts: thread t sums digits DPT t ..
+    // DPT t + DPT - 1, then a block scan of the thread sums
+    int cnt[DPT], tsum = 0;
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+        cnt[j] = running[DPT * threadIdx.x + j];
+        tsum += cnt[j];
+    }
+    int incl = tsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
@@ -178,39 +201,45 @@ __global__ void __launch_bounds__(kT) k_radix_scatter(const int32_t *__restrict_
     }
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-    int before = 0;
-    for (int w = 0; w < warp; ++w) before += wsum[w];
-    const int local_start = before + incl - cnt;
-    const int64_t oi = (int64_t)threadIdx.x * ntiles + blockIdx.x;
-    gshift[threadIdx.x] = offsets[oi] + offset_blocks[oi / kScanBlock] - local_start;
-    running[threadIdx.x] = local_start;
+    int start = incl - tsum;
+    for (int w = 0; w < warp; ++w) start += wsum[w];
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+        const int d = DPT * threadIdx.x + j;
+        const int64_t oi = (int64_t)d * ntiles + blockIdx.x;
+        gshift[d] = offsets[oi] + offset_blocks[oi / kScanBlock] - start;
+        running[d] = start;
+        start += cnt[j];
+    }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kKeysPerThread; ++r) {
         const bool valid = r * kT + (int)threadIdx.x < tile_n;
-        const int digit = valid ? (key[r] >> shift) & 255 : 256;  // 256 never matches a real digit
+        const int digit = valid ? (key[r] >> shift) & (NB - 1) : NB;  // NB never matches a real digit
         const unsigned peers = __match_any_sync(0xFFFFFFFFu, digit);
         const int rank = __popc(peers & ((1u << lane) - 1u));
-        if (valid && rank == 0) wcount[warp][digit] = __popc(peers);
+        if (valid && rank == 0) wcount[warp * NB + digit] = __popc(peers);
         __syncthreads();
         if (valid) {
             int pos = running[digit] + rank;
-            for (int w = 0; w < warp; ++w) pos += wcount[w][digit];
+            for (int w = 0; w < warp; ++w) pos += wcount[w * NB + digit];
             s_key[pos] = key[r];
             s_val[pos] = val[r];
         }
         __syncthreads();
-        int add = 0;
-        for (int w = 0; w < kT / 32; ++w) {
-            add += wcount[w][threadIdx.x];
-            wcount[w][threadIdx.x] = 0;
+        for (int d = threadIdx.x; d < NB; d += kT) {
+            int add = 0;
+            for (int w = 0; w < kT / 32; ++w) {
+                add += wcount[w * NB + d];
+                wcount[w * NB + d] = 0;
+            }
+            running[d] += add;
         }
-        running[threadIdx.x] += add;
         __syncthreads();
     }
     for (int i = threadIdx.x; i < tile_n; i += kT) {
         const int32_t k = s_key[i];
-        const int pos = gshift[(k >> shift) & 255] + i;
+        const int pos = gshift[(k >> shift) & (NB - 1)] + i;
         keys_out[pos] = k;
         vals_out[pos] = s_val[i];
     }
@@ -468,7 +497,7 @@ static gcp_status det_scratch(gcp_ctx *c, int64_t S, size_t *offs) {
     offs[3] = take((size_t)S * 4);                  // vals A
     offs[4] = take((size_t)S * 4);                  // keys B
     offs[5] = take((size_t)S * 4);                  // vals B
-    offs[6] = take((size_t)256 * ntiles * 4);       // digit histograms / offsets
+    offs[6] = take((size_t)1024 * ntiles * 4);      // digit histograms / offsets (up to 1024 digits)
     offs[7] = take((size_t)2 * nchunk * 4);         // carry keys (level in)
     offs[8] = take((size_t)2 * nchunk * c->Rp * 4); // carry vectors (level in)
     offs[9] = take((size_t)2 * nchunk * 4);         // carry keys (level out)
@@ -477,7 +506,7 @@ static gcp_status det_scratch(gcp_ctx *c, int64_t S, size_t *offs) {
     offs[12] = take((size_t)2 * nchunk * 4);        // compacted keys
     offs[13] = take((size_t)2 * nchunk * c->Rp * 4);
     offs[14] = take(16);                            // list length
-    const int64_t scan_n = 256 * ntiles > 2 * nchunk ? 256 * ntiles : 2 * nchunk;
+    const int64_t scan_n = 1024 * ntiles > 2 * nchunk ? 1024 * ntiles : 2 * nchunk;
     offs[15] = take((size_t)((scan_n + kScanBlock - 1) / kScanBlock + 1) * 4);  // scan block sums
     if (o > c->det_scratch_bytes) {
         cudaFree(c->det_scratch);
@@ -525,6 +554,19 @@ static void launch_seg_samples(const SegSpec &P, int cols, int grid, const int32
     }
 }
 
+// The 1024-digit scatter needs more than the default 48 KB of dynamic
+// shared memory; raised once per device.
+static cudaError_t allow_wide_scatter() {
+    static int done_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || done_dev == dev) return e;
+    e = cudaFuncSetAttribute(k_radix_scatter<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem_bytes<1024>());
+    if (e == cudaSuccess) done_dev = dev;
+    return e;
+}
+
 gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     const int64_t S = f0.s.p + f0.s.q;
     size_t offs[16];
@@ -546,6 +588,7 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     int32_t *dlen = reinterpret_cast<int32_t *>(base + offs[14]);
     int32_t *bsum = reinterpret_cast<int32_t *>(base + offs[15]);
     cudaStream_t st = c->st;
+    DET_CUDA(allow_wide_scatter());
 
     // 1. loss partials and the materialised gradient tensor
     gcpk::FusedSpec f = f0;
@@ -579,11 +622,19 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
         int kstride = c->d;
         const int32_t *vin = nullptr;
         int32_t *kout = kA, *vout = vA;
-        for (int shift = 0; shift < bits; shift += 8) {
-            k_radix_hist<<<(int)ntiles, kT, 0, st>>>(kin, kstride, S, shift, hist, (int)ntiles);
-            scan_two_part(hist, hist, 256 * ntiles, false, nullptr, bsum, st);
-            k_radix_scatter<<<(int)ntiles, kT, 0, st>>>(kin, kstride, vin, S, shift, hist, bsum, (int)ntiles, kout,
-                                                        vout);
+        const bool wide = bits > 8 && bits <= 10;  // one 10-bit pass instead of 8 + 2
+        for (int shift = 0; shift < bits; shift += wide ? 10 : 8) {
+            if (wide) {
+                k_radix_hist<1024><<<(int)ntiles, kT, 0, st>>>(kin, kstride, S, shift, hist, (int)ntiles);
+                scan_two_part(hist, hist, 1024 * ntiles, false, nullptr, bsum, st);
+                k_radix_scatter<1024><<<(int)ntiles, kT, scatter_smem_bytes<1024>(), st>>>(
+                    kin, kstride, vin, S, shift, hist, bsum, (int)ntiles, kout, vout);
+            } else {
+                k_radix_hist<256><<<(int)ntiles, kT, 0, st>>>(kin, kstride, S, shift, hist, (int)ntiles);
+                scan_two_part(hist, hist, 256 * ntiles, false, nullptr, bsum, st);
+                k_radix_scatter<256><<<(int)ntiles, kT, scatter_smem_bytes<256>(), st>>>(
+                    kin, kstride, vin, S, shift, hist, bsum, (int)ntiles, kout, vout);
+            }
             DET_CUDA(cudaGetLastError());
             kin = kout;
             vin = vout;
