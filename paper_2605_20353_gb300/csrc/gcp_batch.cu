@@ -398,10 +398,10 @@ __device__ __forceinline__ void fold_quad(const ClientAux &a, int hs, int col, f
 // cleared), then Algorithm 1 on the four entries.  G itself is cleared at
 // the start of the next step, just before the fused pass, so that its lines
 // are still in L2 when the reductions arrive.
-constexpr int kPostUnroll = 2;
+constexpr int kPostUnroll = 1;  // one quad per thread, six blocks per SM (fastest measured)
 constexpr int kPostQuads = kPostUnroll * kThreads;
 
-__global__ void __launch_bounds__(kThreads, 4) k_batch_post(const ClientAux *__restrict__ aux,
+__global__ void __launch_bounds__(kThreads, 6) k_batch_post(const ClientAux *__restrict__ aux,
                                                             const int2 *__restrict__ chunks,
                                                             const float2 *__restrict__ tile_loss, double *client_loss,
                                                             const double *__restrict__ adam) {
