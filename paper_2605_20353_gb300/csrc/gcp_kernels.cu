@@ -500,6 +500,8 @@ __global__ void k_adam(int64_t n, int Rp, int R, float *__restrict__ A, float *_
 // the others take every element of the flat parameter vector: its gradient
 // (adding the replicas of a hot row and clearing them), Algorithm 1, and G
 // cleared for the next step.
+constexpr int kPostFold = 16;  // replica loads of a hot element in flight at a time
+
 __global__ void __launch_bounds__(kThreads) k_post_step(PostSpec P) {
     if (blockIdx.x == gridDim.x - 1) {  // the last block only finishes the loss
         __shared__ double sh[3][kThreads];
@@ -531,16 +533,16 @@ __global__ void __launch_bounds__(kThreads) k_post_step(PostSpec P) {
         float g = P.G[e];
         const float b0 = P.B[e], c0 = P.C[e], a0 = P.A[e];
         const int hs = P.hot_slot ? __ldg(P.hot_slot + row) : -1;
-        if (hs >= 0) {  // replicas added in replica order, 16 loads in flight at a time, then cleared
+        if (hs >= 0) {  // replicas added in replica order, kPostFold loads in flight at a time, then cleared
             const int64_t o = (int64_t)hs * P.Rp + col;
-            for (int r0 = 0; r0 < kReplicas; r0 += 16) {
-                float v[16];
+            for (int r0 = 0; r0 < kReplicas; r0 += kPostFold) {
+                float v[kPostFold];
 #pragma unroll
-                for (int r = 0; r < 16; ++r) v[r] = P.Grep[(r0 + r) * plane + o];
+                for (int r = 0; r < kPostFold; ++r) v[r] = P.Grep[(r0 + r) * plane + o];
 #pragma unroll
-                for (int r = 0; r < 16; ++r) g += v[r];
+                for (int r = 0; r < kPostFold; ++r) g += v[r];
 #pragma unroll
-                for (int r = 0; r < 16; ++r) P.Grep[(r0 + r) * plane + o] = 0.0f;
+                for (int r = 0; r < kPostFold; ++r) P.Grep[(r0 + r) * plane + o] = 0.0f;
             }
         }
         P.G[e] = 0.0f;
