@@ -12,8 +12,9 @@ Parity pins live in ``tests/test_oracle_pins.py``: Philox against numpy's
 independent Philox4x64-10, the losses against scipy.stats negative
 log-likelihoods, the full gradient against the Gaussian closed form and an
 einsum MTTKRP, the stratified estimator's expectation by exact enumeration,
-central finite differences, the sampler's distribution, and Adam against
-torch.optim.Adam.
+central finite differences, the samplers' distributions, weights and counter
+layout (the semi-stratified sampler's included, against numpy's Philox),
+and Adam against torch.optim.Adam.
 """
 from __future__ import annotations
 

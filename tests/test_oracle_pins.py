@@ -278,6 +278,87 @@ def test_sampler_distribution_chi_square():
     assert abs(attempts / q - mean) < 5 * math.sqrt(var / q)
 
 
+def _counter_draw(seed, stream, t, j, sub0, dims):
+    """A coordinate tuple of the documented counter layout, computed with
+    numpy's independent Philox4x64-10 and Python integers: key (seed,
+    stream), counter (j, sub0 + b, t, 0) for modes 4b..4b+3, word u of mode
+    k mapped onto [0, I_k) as floor(u I_k / 2^64)."""
+    out = []
+    for b in range((len(dims) + 3) // 4):
+        words = _numpy_philox_block((j, sub0 + b, t, 0), (seed, stream))
+        for k in range(4 * b, min(len(dims), 4 * b + 4)):
+            out.append(int(words[k - 4 * b]) * int(dims[k]) >> 64)
+    return out
+
+
+def test_semi_stratified_sampler_weights_values_and_layout():
+    """Semi-stratified sample set (Sec. 3.1.1), checked without the GPU:
+    nonzero samples are records with weight N/p; zero candidates carry x = 0
+    and weight M/q (drawn over all M cells, so the unbiased weight is M/q,
+    not (M-N)/q); flags mark the nonzeros; and the draws follow the counter
+    layout (stream 0 for nonzeros, stream 3 for zero candidates) computed
+    independently with numpy's Philox."""
+    w = synth.workload_small_gaussian()
+    dims, coords, vals = w["dims"], w["coords"], w["vals"]
+    N, M = len(vals), int(np.prod(dims))
+    seed, t, p, q = 3101, 9, 700, 900
+    idx, x, wts, semi = oracle.semi_stratified_samples(seed, t, p, q, dims, coords, vals)
+    assert np.all(wts[:p] == N / p)
+    assert np.all(wts[p:] == M / q) and M / q != (M - N) / q
+    assert np.all(semi[:p] == 1) and np.all(semi[p:] == 0)
+    assert np.all(x[p:] == 0.0)
+    for j in range(p):  # nonzero j: record e = floor(u N / 2^64) of stream 0
+        e = int(_numpy_philox_block((j, 0, t, 0), (seed, 0))[0]) * N >> 64
+        assert idx[j].tolist() == coords[e].tolist() and x[j] == float(vals[e])
+    for j in range(q):
+        assert idx[p + j].tolist() == _counter_draw(seed, 3, t, j, 0, dims)
+
+
+def test_semi_stratified_zero_candidates_cover_every_cell():
+    """Zero candidates of the semi-stratified sampler are uniform over all M
+    cells, nonzero cells included: no rejection (Sec. 3.1.1).  Chi-square
+    over the 60,000 cells of the 50 x 40 x 30 tensor, and the share of
+    candidates that land on one of its 2,000 nonzeros is N/M."""
+    w = synth.workload_small_gaussian()
+    dims, coords, vals = w["dims"], w["coords"], w["vals"]
+    N, M = len(vals), int(np.prod(dims))
+    q = 20 * M
+    idx, x, wts, _ = oracle.semi_stratified_samples(3102, 4, 0, q, dims, coords, vals)
+    keys = np.zeros(q, dtype=np.int64)
+    for k in range(3):
+        keys = keys * dims[k] + idx[:, k]
+    counts = np.bincount(keys, minlength=M)
+    assert counts.size == M
+    assert scipy.stats.chisquare(counts).pvalue > 1e-4
+    on_nz = np.isin(keys, oracle.sorted_keys(dims, coords).astype(np.int64)).sum()
+    share = N / M
+    assert abs(on_nz / q - share) < 5 * math.sqrt(share * (1 - share) / q)
+    assert on_nz > 0.9 * share * q  # a rejecting sampler would give none
+
+
+def test_stratified_sampler_follows_counter_layout():
+    """Stratified draws (Sec. 3.1.1) against numpy's Philox: nonzero j is
+    record floor(u N / 2^64) of stream 0; zero draw j takes the first
+    attempt a whose stream-1 tuple at sub-counter 4a is not a nonzero."""
+    w = synth.workload_small_gaussian()
+    dims, coords, vals = w["dims"], w["coords"], w["vals"]
+    N = len(vals)
+    seed, t, p, q = 3103, 2, 300, 400
+    idx, x, _, _ = oracle.stratified_samples(seed, t, p, q, dims, coords, vals)
+    for j in range(p):
+        e = int(_numpy_philox_block((j, 0, t, 0), (seed, 0))[0]) * N >> 64
+        assert idx[j].tolist() == coords[e].tolist() and x[j] == float(vals[e])
+    nz = {tuple(c) for c in coords.tolist()}
+    redrawn = 0
+    for j in range(q):
+        a = 0
+        while tuple(cand := _counter_draw(seed, 1, t, j, 4 * a, dims)) in nz:
+            a += 1
+        redrawn += a > 0
+        assert idx[p + j].tolist() == cand
+    assert redrawn > 0  # the redraw path is exercised (about 3% of draws)
+
+
 def test_sampler_reproducible_and_iteration_dependent():
     w = synth.workload_small_gaussian()
     a = oracle.stratified_samples(7, 3, 50, 50, w["dims"], w["coords"], w["vals"])
