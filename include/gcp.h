@@ -359,7 +359,9 @@ gcp_status gcp_batch_server_step(gcp_batch *batch, const gcp_adam_params *prm, i
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture.  Every call on a device
  * shares the array: calls whose kernels overlap on the GPU race and must be
- * ordered by the caller (one stream, or events).  Asynchronous. */
+ * ordered by the caller (one stream, or events).  Asynchronous: the call
+ * returns before any result exists, so a NaN or infinite loss is not a
+ * status code here; the caller reads loss_out[0] after the stream. */
 #define GCP_NOALLOC_MAX_SAMPLES 16777216LL
 gcp_status gcp_grad_samples_noalloc(int32_t ndim, const int64_t *dims, int32_t rank, int32_t loss,
                                     int64_t nsamples, const int32_t *idx, const float *x, const float *w,

@@ -441,6 +441,12 @@ def test_zipf_count_full_size(env, zipf_full, dtype, tol):
         Lf, Gf = oracle.sampled_loss_grad(w["dims"], w["factors"], "poisson", idx, x, wt)
         assert abs(Lg - Lf) <= TOL_BF16 * abs(Lf)
         assert rel_err(Gg, np.concatenate([g.ravel() for g in Gf])) <= TOL_BF16
+    # the timed step (gcp_step: fused pass + epilogue with the replica fold)
+    # consumes the same gradient
+    g_max = max(np.abs(g).max() for g in Go)
+    Gs = step_gradient(gcp, ctx, w["factors"], 5, w["p"], w["q"], g_max)
+    for n, (a, b) in enumerate(zip(split(Gs, w["dims"], 32), Go)):
+        assert rel_err(a, b) <= tol, (dtype, "step", n, rel_err(a, b))
     ctx.close()
 
 
@@ -582,6 +588,40 @@ def test_step_equals_grad_then_adam_and_oracle(env, dtype):
     assert rel_err(fa, fb) <= TOL_FP32
     a.close()
     b.close()
+
+
+def step_gradient(gcp, ctx, factors, it, p, q, g_max):
+    """The gradient that one gcp_step of iteration `it` folds and feeds to
+    Adam, read back through a readout Adam step (tests/adam_readout.py)."""
+    from adam_readout import flat, readout_params, recover_gradient
+
+    prm = readout_params(gcp, g_max)
+    ctx.set_factors(factors)
+    ctx.reset_adam()
+    ctx.step(it, p, q, prm, 1)
+    ctx.sync()
+    return recover_gradient(flat(factors), flat(ctx.get_factors()), prm)
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "bf16"])
+def test_step_folded_gradient_matches_oracle(env, dtype):
+    """The gradient inside gcp_step (fused pass, then the epilogue's replica
+    fold) element by element against the oracle's sampled gradient (Eq.
+    gcp-gradient), per mode, at 1e-5.  The Zipf tensor's 200-row mode is
+    fully replicated, its other modes have replicated head rows carried in
+    the nonzero records, and drawn zero cells reach unreplicated rows."""
+    gcp, torch = env
+    w = synth.workload_zipf_count(scale=0.01)
+    dims, p, q, R = w["dims"], 9000, 9001, 32
+    ctx = gcp.gcp_create(dims, w["coords"], w["vals"], R, "poisson", dtype=dtype, seed=53)
+    fac = [bf16_round(x) for x in w["factors"]] if dtype == "bf16" else w["factors"]
+    idx, x, wt, _ = oracle.stratified_samples(53, 2, p, q, dims, w["coords"], w["vals"])
+    _, Go = oracle.sampled_loss_grad(dims, fac, "poisson", idx, x, wt)
+    g_max = max(np.abs(g).max() for g in Go)
+    G = step_gradient(gcp, ctx, w["factors"], 2, p, q, g_max)
+    for n, (a, b) in enumerate(zip(split(G, dims, R), Go)):
+        assert rel_err(a, b) <= TOL_FP32, (dtype, n, rel_err(a, b))
+    ctx.close()
 
 
 def test_fit_with_tuned_preset_on_count_data(env):

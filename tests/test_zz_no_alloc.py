@@ -71,3 +71,49 @@ def test_noalloc_rejects_more_samples_than_its_scratch_holds(env):
     rc = lib.gcp_grad_samples_noalloc(3, d.ctypes.data, 2, 1, (1 << 24) + 1, 1, 1, 1, 1, 1, 1, None)
     assert rc == 1
     assert b"GCP_NOALLOC_MAX_SAMPLES" in lib.gcp_last_error(None)
+
+
+@pytest.mark.parametrize("loss", ["gaussian", "poisson", "bernoulli", "gamma"])
+def test_noalloc_skips_out_of_range_samples(env, loss):
+    """Samples with a coordinate outside its mode (negative or past the end)
+    are skipped and counted in loss_out[1]; the loss and gradient are those
+    of the in-range samples, against the FP64 oracle on that subset, for
+    every loss."""
+    import oracle
+
+    gcp, torch = env
+    dims, R = [50, 40, 30], 12
+    coords, vals = synth.uniform_sparse(dims, 2500, 920, lam=2.0)
+    if loss == "bernoulli":
+        vals = np.ones_like(vals)
+    if loss in ("gaussian", "bernoulli"):
+        factors = synth.factors_normal(dims, R, 921, std=0.6)
+    else:
+        factors = synth.factors_uniform(dims, R, 921, lo=0.1, hi=1.0)
+    ctx = gcp.gcp_create(dims, coords, vals, R, loss, seed=922)
+    idx, x, w = ctx.sample(6, 1500, 1700)
+    idx_h = idx.cpu().numpy().copy()
+    rng = np.random.default_rng(923)
+    bad = np.sort(rng.choice(idx_h.shape[0], 37, replace=False))
+    for j, s in enumerate(bad):  # one coordinate off the end or negative, in varying modes
+        k = j % 3
+        idx_h[s, k] = dims[k] + j if j % 2 else -1 - j
+    A = torch.from_numpy(np.concatenate([a.ravel() for a in factors])).cuda()
+    G = torch.full((ctx.num_params,), float("nan"), device="cuda")
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    idx_d = torch.from_numpy(idx_h).cuda()
+    lib = gcp.load()
+    d = np.array(dims, dtype=np.int64)
+    rc = lib.gcp_grad_samples_noalloc(3, d.ctypes.data, R, gcp.LOSSES[loss], idx_h.shape[0], idx_d.data_ptr(),
+                                      x.data_ptr(), w.data_ptr(), A.data_ptr(), G.data_ptr(), out.data_ptr(),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, lib.gcp_last_error(None)
+    torch.cuda.synchronize()
+    L, skipped = out.cpu().numpy()
+    assert skipped == len(bad)
+    keep = np.setdiff1d(np.arange(idx_h.shape[0]), bad)
+    Lo, Go = oracle.sampled_loss_grad(dims, factors, loss, idx_h[keep], x.cpu().numpy()[keep].astype(np.float64),
+                                      w.cpu().numpy()[keep].astype(np.float64))
+    assert abs(L - Lo) <= TOL * abs(Lo), (L, Lo)
+    assert rel_err(G.cpu().numpy(), np.concatenate([g.ravel() for g in Go])) <= TOL
+    ctx.close()
