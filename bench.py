@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 METRIC = "GCP gradient samples/s & % HBM peak; BF16/batched vs plain FP32 at rel-err≤5e-3"
 WORKLOAD = ("zipf-count 4-way 2000x1500x1000x200, 5e7 nnz Zipf(1.1) coords, 1+Poisson(3) values, "
             "Poisson loss, rank 32, p=q=2^20 stratified samples")
+# what stays resident where; both arms print the same config
+L2_NOTE = ("inputs larger than L2 (1.6 GB records, 2.1 GB hash set); factors and gradient (0.6 MB each) stay "
+           "L2-resident across steps as in training")
+CONFIG = {"workload": WORKLOAD, "l2": L2_NOTE}
 KERNEL_SOURCES = ["paper_2605_20353_gb300/csrc/gcp_kernels.cu", "paper_2605_20353_gb300/csrc/gcp_device.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_grad_zipf_count_traffic.json")
 
@@ -55,6 +59,16 @@ def algorithmic_bytes_per_sample(d, R, nnz, M, elt_bytes):
     attempts = 1.0 / (1.0 - nnz / M)
     rows = d * R * (elt_bytes + 4)
     return 0.5 * (4 * (d + 1) + rows) + 0.5 * (32 * attempts + rows)
+
+
+def compulsory_bytes_per_sample(d, R, nnz, M, rows, elt_bytes=4):
+    """HBM bytes a sample cannot avoid when the model stays in L2: one 32-byte
+    sector for a nonzero's record, one 32-byte bucket sector per rejection
+    attempt for a zero, plus the model (factors read, gradient read and
+    written once per step: rows x R x 3 x 4 B) spread over the step's 2^21
+    samples."""
+    attempts = 1.0 / (1.0 - nnz / M)
+    return 0.5 * 32 + 0.5 * 32 * attempts + rows * R * (elt_bytes + 8) / float(1 << 21)
 
 
 # the fused pass's part of gcp_kernels.cu ends where the replica fold begins
@@ -286,7 +300,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "samples_per_step": per_step},
+            "config": dict(CONFIG),
+            "step": {"what": "the FP64 oracle (stratified sampling, loss, all-mode gradient) on a bounded sample "
+                             "of the workload, split over the host cores", "samples": per_step},
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} samples per step of the same workload ({per_core} per core, "
                                        f"{cores} spawned processes, each on its own iteration)"},
@@ -369,26 +385,38 @@ def batched_variant(gcp, torch, stream, steps=20, with_oracle=True):
     batch.close()
     for c in clients:
         c.close()
-    for dtype in ("bf16", "fp32"):
-        clients = make(dtype)
-        for i, c in enumerate(clients):
-            c.grad_async(0, P[i], P[i])
-            c.adam_step(adam, 1)
-        stream.synchronize()
-        nseq = max(2, steps // 4)
-        e0.record(stream)
-        for k in range(nseq * tau):
+    # 64 sequential single-client steps: gcp_step (fused pass + one epilogue,
+    # two launches per client, the best single-client path) and gradient +
+    # Adam as separate calls (five launches per client)
+    nseq = max(2, steps // 4)
+    for form in ("step", "grad_adam"):
+        for dtype in ("bf16", "fp32"):
+            clients = make(dtype)
             for i, c in enumerate(clients):
-                c.grad_async(k + 1, P[i], P[i])
-                c.adam_step(adam, k + 2)
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        res[f"sequential_{dtype}"] = {"value": samples_per_step * tau * nseq / (ms / 1e3), "unit": "samples/s"}
-        for c in clients:
-            c.close()
-    res["speedup_vs_sequential_bf16"] = res["batched_graph"]["value"] / res["sequential_bf16"]["value"]
-    res["speedup_vs_sequential_fp32"] = res["batched_graph"]["value"] / res["sequential_fp32"]["value"]
+                if form == "step":
+                    c.step(0, P[i], P[i], adam, 1)
+                else:
+                    c.grad_async(0, P[i], P[i])
+                    c.adam_step(adam, 1)
+            stream.synchronize()
+            e0.record(stream)
+            for k in range(nseq * tau):
+                for i, c in enumerate(clients):
+                    if form == "step":
+                        c.step(k + 1, P[i], P[i], adam, k + 2)
+                    else:
+                        c.grad_async(k + 1, P[i], P[i])
+                        c.adam_step(adam, k + 2)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            key = f"sequential_{form}_{dtype}"
+            res[key] = {"value": samples_per_step * tau * nseq / (ms / 1e3), "unit": "samples/s",
+                        "launches_per_client_step": 2 if form == "step" else 5}
+            for c in clients:
+                c.close()
+    for key in [k for k in res if k.startswith("sequential_")]:
+        res["speedup_vs_" + key] = res["batched_graph"]["value"] / res[key]["value"]
     return res
 
 
@@ -412,6 +440,7 @@ def hbm_resident_variant(gcp, torch, stream, launches=20, dtypes=("fp32", "bf16"
 
     w = synth.cached("hbm_resident_amazon_dims", gen)
     S = 1 << 20
+    adam = gcp.AdamParams(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, lower=0.0)
     res = {"workload": "4.8Mx1.7Mx1.1M, 2e7 uniform nnz, Poisson, p=q=2^20; rank 16 (factors 486 MB FP32) "
                        "and rank 32 (973 MB)"}
     for R in ranks:
@@ -428,13 +457,34 @@ def hbm_resident_variant(gcp, torch, stream, launches=20, dtypes=("fp32", "bf16"
             for i in range(launches):
                 ctx.grad_async(100 + i, S, S)
             kms, nl = ctx.profile_read()
+            # the whole training step (gcp_step: fused pass + the epilogue
+            # that streams every parameter through Adam), CUDA events
+            for i in range(3):
+                ctx.step(200 + i, S, S, adam, i + 1)
+            ctx.profile_read()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(launches):
+                ctx.step(300 + i, S, S, adam, 4 + i)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms = e0.elapsed_time(e1) / launches
+            skms, snl = ctx.profile_read()
             ctx.profile(False)
+            nparam = ctx.num_params
             ctx.close()
             per = kms / nl
             bps = algorithmic_bytes_per_sample(3, R, len(w["vals"]), float(np.prod(dims, dtype=np.float64)),
                                                4 if dtype == "fp32" else 2)
+            epi_ms = step_ms - skms / max(1, snl)
+            # epilogue bytes per parameter: G, A, B, C read; A, B, C written,
+            # G cleared; the BF16 copy written when there is one
+            epi_bytes = nparam * (32 + (2 if dtype == "bf16" else 0))
             out[dtype] = {"kernel_ms_per_launch": per, "samples_per_s": 2 * S / (per / 1e3),
-                          "achieved_gbs": bps * 2 * S / (per / 1e3) / 1e9, "bytes_per_sample": bps}
+                          "achieved_gbs": bps * 2 * S / (per / 1e3) / 1e9, "bytes_per_sample": bps,
+                          "step_ms": step_ms, "step_samples_per_s": 2 * S / (step_ms / 1e3),
+                          "epilogue_ms": epi_ms, "epilogue_bytes": epi_bytes,
+                          "epilogue_gbs": epi_bytes / (epi_ms / 1e3) / 1e9 if epi_ms > 0 else None}
         if "fp32" in out and "bf16" in out:
             out["bf16_speedup"] = out["fp32"]["kernel_ms_per_launch"] / out["bf16"]["kernel_ms_per_launch"]
     return res
@@ -815,40 +865,49 @@ def run_ours(args):
     bps = algorithmic_bytes_per_sample(4, R, len(w["vals"]), float(np.prod(dims, dtype=np.float64)), 4)
     bps_bf = algorithmic_bytes_per_sample(4, R, len(w["vals"]), float(np.prod(dims, dtype=np.float64)), 2)
     kernel_avg_s = kernel_ms / 1e3 / launches
-    achieved = bps * S / kernel_avg_s / 1e9
-    l2_bytes = measured_traffic("lts_bytes_per_launch")
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": measured_traffic(), "kernel": "k_fused<4,float>",
-                "bytes_per_sample": bps, "kernel_ms_per_launch": kernel_avg_s * 1e3,
-                "peak_source": f"{peak_kind} HBM copy bandwidth",
-                # the factor and gradient rows are L2-resident, so L2 serves most
-                # of the logical bytes: L2 traffic of the same ncu capture, over
-                # the live kernel time, with the capture's own utilisation figures
-                "l2": {"traffic": l2_bytes, "unit": "GB/s",
-                       "achieved": l2_bytes / kernel_avg_s / 1e9 if l2_bytes else None,
-                       "lts_sectors_pct_of_peak": measured_traffic("lts_sectors_pct_of_peak"),
-                       "lts_throughput_pct_of_peak": measured_traffic("lts_throughput_pct_of_peak"),
-                       "l1tex_throughput_pct_of_peak": measured_traffic("l1tex_throughput_pct_of_peak")}}
-    # the binding limit: the fused pass's gathers and reductions against the
-    # same row traffic measured alone on an L2-resident buffer
+    # The binding resource: the factor and gradient rows are L2-resident, so
+    # the fused pass is bound by its row traffic between the SMs and L2
+    # (d = 4 rows of 128 B gathered and 4 reduced per sample).  Its ceiling
+    # is the same row operations alone on uniformly random rows of an
+    # L2-resident buffer (gcp_probe_l2), measured in this run.
     ceil = l2_ceiling(gcp, torch, stream, 4, 32, S)
-    red_bytes = S * 4 * 32 * 4
-    roofline["l2_rows"] = {
-        "what": "fused pass's factor-row gathers + gradient-row reductions (d=4 rows of 128 B each per sample) "
-                "vs the same row operations alone on uniformly random rows of an L2-resident buffer "
-                "(gcp_probe_l2, measured in this run)",
-        "achieved": 2 * red_bytes / kernel_avg_s / 1e9, "peak": ceil["both"]["gbs"], "unit": "GB/s",
-        "frac": (2 * red_bytes / kernel_avg_s / 1e9) / ceil["both"]["gbs"],
-        "reductions_achieved": red_bytes / kernel_avg_s / 1e9, "reductions_peak": ceil["red"]["gbs"],
-        "reductions_frac": (red_bytes / kernel_avg_s / 1e9) / ceil["red"]["gbs"], "probe": ceil}
+    row_bytes = 2 * S * 4 * 32 * 4
+    achieved = row_bytes / kernel_avg_s / 1e9
+    dram = measured_traffic()
+    compulsory = compulsory_bytes_per_sample(4, R, len(w["vals"]), float(np.prod(dims, dtype=np.float64)),
+                                             sum(dims))
+    roofline = {"bound": "l2", "achieved": achieved, "peak": ceil["both"]["gbs"], "unit": "GB/s",
+                "frac": achieved / ceil["both"]["gbs"], "traffic": dram, "kernel": "k_fused<4,float,4>",
+                "kernel_ms_per_launch": kernel_avg_s * 1e3,
+                "what": "fused pass's factor-row gathers + gradient-row reductions (4 rows of 128 B each per sample) "
+                        "per launch / its CUDA-event time, against the same row operations alone on uniformly "
+                        "random rows of an L2-resident buffer (gcp_probe_l2, measured in this run: a builder-"
+                        "measured ceiling, not a driver peak); traffic = ncu DRAM bytes per launch",
+                "peak_source": "gcp_probe_l2 'both' rate, this run",
+                "reductions": {"achieved": row_bytes / 2 / kernel_avg_s / 1e9, "peak": ceil["red"]["gbs"],
+                               "frac": (row_bytes / 2 / kernel_avg_s / 1e9) / ceil["red"]["gbs"]},
+                "probe": ceil,
+                # HBM: what the kernel moves through DRAM (ncu bytes per launch
+                # over the live kernel time), against the measured copy peak
+                "hbm": {"achieved": dram / kernel_avg_s / 1e9 if dram else None, "peak": peak, "unit": "GB/s",
+                        "frac": dram / kernel_avg_s / 1e9 / peak if dram else None,
+                        "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                        "dram_bytes_per_sample": dram / S if dram else None,
+                        "compulsory_bytes_per_sample": compulsory,
+                        "dram_over_compulsory": dram / S / compulsory if dram else None},
+                # the scope table's logical bytes (record or bucket, gathers,
+                # reductions) over the kernel time: most are served by L2, so
+                # this is not an HBM fraction
+                "logical": {"bytes_per_sample": bps, "achieved": bps * S / kernel_avg_s / 1e9, "unit": "GB/s",
+                            "over_hbm_peak": bps * S / kernel_avg_s / 1e9 / peak}}
     base = cpu_baseline(w)
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "samples_per_step": S, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (1.6 GB records, 2.1 GB hash set); factors and gradient "
-                             "(0.6 MB each) stay L2-resident across steps as in training",
-                       "step": "gcp_step: fused sampled gradient + one epilogue (loss, replica fold, Adam)"},
+            "config": dict(CONFIG),
+            "step": {"what": "gcp_step: fused sampled gradient (sampling, model, loss, all-mode MTTKRP) + one "
+                             "epilogue (loss finish, replica fold, Adam)", "samples": S,
+                     "parallelism": f"replicas{world}"},
             "roofline": roofline, "cpu_baseline": base,
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(A_host.numel() * 4),
                     "d2h_bytes_per_step": int(G_host.numel() * 4 + 8)},

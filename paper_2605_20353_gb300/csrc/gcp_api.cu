@@ -373,6 +373,7 @@ gcp_status do_step(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, const gcp_ad
     ps.C = c->C;
     ps.Abf = c->Abf;
     ps.hot_slot = c->hot_slot;
+    ps.hot_row = c->hot_row;
     ps.lr = (float)prm->lr;
     ps.beta1 = (float)prm->beta1;
     ps.beta2 = (float)prm->beta2;

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "gcp_device.cuh"
+#include "gcp_epilogue.cuh"
 #include "gcp_internal.h"
 
 using namespace gcpdev;
@@ -369,81 +370,93 @@ __device__ __forceinline__ void adam_quad(const ClientAux &a, int64_t qi, int co
     }
 }
 
-// Hot row: add its kReplicas replica quads to g4 in replica order, then
-// clear them for the next step.
-__device__ __forceinline__ void fold_quad(const ClientAux &a, int hs, int col, float4 &g4) {
-    const int64_t plane4 = ((int64_t)a.Htot * a.Rp) >> 2, o = ((int64_t)hs * a.Rp + col) >> 2;
-    float4 *R4 = reinterpret_cast<float4 *>(a.Grep);
-    for (int r0 = 0; r0 < gcpk::kReplicas; r0 += 8) {
-        float4 v[8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) v[r] = R4[(r0 + r) * plane4 + o];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            g4.x += v[r].x;
-            g4.y += v[r].y;
-            g4.z += v[r].z;
-            g4.w += v[r].w;
-        }
-#pragma unroll
-        for (int r = 0; r < 8; ++r) R4[(r0 + r) * plane4 + o] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    }
-}
-
 // The epilogue of one local step of every client, one launch over a chunk
-// list built at batch creation.  A chunk {client, -1} finishes that client's
-// loss; a chunk {client, q} takes the client's parameter quads q ..
-// q + kPostQuads - 1, kPostUnroll per thread with all gradient loads issued first:
-// the gradient quad plus, for a hot row, its replica quads (replicas
-// cleared), then Algorithm 1 on the four entries.  G itself is cleared at
-// the start of the next step, just before the fused pass, so that its lines
-// are still in L2 when the reductions arrive.
-constexpr int kPostUnroll = 1;  // one quad per thread, six blocks per SM (fastest measured)
-constexpr int kPostQuads = kPostUnroll * kThreads;
+// list built at batch creation.  A chunk {client, code} is
+//  - code == -1: finish that client's loss;
+//  - code >= 0: the client's parameter quads code .. code + kThreads - 1,
+//    one per thread, all loads (gradient, moments, factor, replica slot)
+//    issued before any is used, then Algorithm 1; quads of hot rows are
+//    left to the hot chunks;
+//  - code <= -2: the client's hot quads h .. h + kThreads / kHotLanes - 1
+//    (h = -2 - code; hot quad h is column quad h % (Rp/4) of replica slot
+//    h / (Rp/4)), one per group of kHotLanes lanes: the group loads all
+//    replica quads at once (gcpe::hot_quad_sum, which clears them), its
+//    first lane adds them to the gradient quad and applies Algorithm 1.
+// G itself is cleared at the start of the next step, just before the fused
+// pass, so that its lines are still in L2 when the reductions arrive.
+// Quads per thread of a streaming chunk, all loads issued together: four
+// measured 0.383 ms per local step of the 64-client batch, against 0.414
+// and 0.418 ms with one and two.
+constexpr int kPostUnroll = 4;
+constexpr int kPostQuads = kThreads * kPostUnroll;              // quads of a streaming chunk
+constexpr int kHotQuadsPerChunk = kThreads / gcpe::kHotLanes;   // hot quads of a hot chunk
+static_assert(gcpk::kReplicas % gcpe::kHotLanes == 0, "hot-quad replicas split evenly over the folding lanes");
 
-__global__ void __launch_bounds__(kThreads, 6) k_batch_post(const ClientAux *__restrict__ aux,
-                                                            const int2 *__restrict__ chunks,
-                                                            const float2 *__restrict__ tile_loss, double *client_loss,
-                                                            const double *__restrict__ adam) {
+__global__ void __launch_bounds__(kThreads) k_batch_post(const ClientAux *__restrict__ aux,
+                                                         const int2 *__restrict__ chunks,
+                                                         const float2 *__restrict__ tile_loss, double *client_loss,
+                                                         const double *__restrict__ adam) {
     const int2 ch = chunks[blockIdx.x];
     const ClientAux &a = aux[ch.x];
-    if (ch.y < 0) {
+    if (ch.y == -1) {
         finish_client_loss(a, tile_loss, client_loss + ch.x);
         return;
     }
     const AdamConsts k{(float)adam[0], (float)adam[1], (float)adam[2], (float)adam[3],
                        (float)adam[4], (float)adam[5], (float)adam[6]};
     const int log2Rp = __ffs(a.Rp) - 1;  // Rp is a power of two and a multiple of 4
+    const float4 *__restrict__ G4 = reinterpret_cast<const float4 *>(a.G);
+    const float4 *__restrict__ A4 = reinterpret_cast<const float4 *>(a.A);
+    const float4 *__restrict__ B4 = reinterpret_cast<const float4 *>(a.B);
+    const float4 *__restrict__ C4 = reinterpret_cast<const float4 *>(a.C);
+    if (ch.y <= -2) {  // hot quads, one per group of kHotLanes lanes
+        const int log2Q = log2Rp - 2;
+        const int64_t hq = (int64_t)(-2 - ch.y) + threadIdx.x / gcpe::kHotLanes;
+        if (hq >= ((int64_t)a.Htot << log2Q)) return;  // the whole group leaves together
+        const int slot = (int)(hq >> log2Q), cq = (int)(hq & ((1 << log2Q) - 1));
+        const int64_t q = ((int64_t)__ldg(a.hot_row + slot) << log2Q) + cq;
+        const bool lead = (threadIdx.x & (gcpe::kHotLanes - 1)) == 0;
+        float4 g4, b4, c4, x4;
+        if (lead) {
+            g4 = G4[q];
+            b4 = B4[q];
+            c4 = C4[q];
+            x4 = A4[q];
+        }
+        const float4 t = gcpe::hot_quad_sum<gcpk::kReplicas>(reinterpret_cast<float4 *>(a.Grep),
+                                                             ((int64_t)a.Htot * a.Rp) >> 2, hq,
+                                                             gcpe::hot_group_mask());
+        const int col = cq << 2;
+        if (!lead || col >= a.R) return;
+        g4.x += t.x;
+        g4.y += t.y;
+        g4.z += t.z;
+        g4.w += t.w;
+        adam_quad(a, q, col, g4, b4, c4, x4, k);
+        return;
+    }
     const int64_t nq = a.nparam >> 2;
-    int64_t q[kPostUnroll];
-#pragma unroll
-    for (int u = 0; u < kPostUnroll; ++u) q[u] = (int64_t)ch.y + threadIdx.x + u * kThreads;
-    const float4 *G4 = reinterpret_cast<const float4 *>(a.G);
-    float4 g4[kPostUnroll];
-    int col[kPostUnroll], hs[kPostUnroll];
+    float4 g4[kPostUnroll], b4[kPostUnroll], c4[kPostUnroll], x4[kPostUnroll];
+    int hs[kPostUnroll];
 #pragma unroll
     for (int u = 0; u < kPostUnroll; ++u) {
-        col[u] = (int)((q[u] << 2) & (a.Rp - 1));
-        hs[u] = -1;
-        if (q[u] < nq) {
-            g4[u] = G4[q[u]];
-            if (a.hot_slot) hs[u] = __ldg(a.hot_slot + ((q[u] << 2) >> log2Rp));
+        const int64_t q = (int64_t)ch.y + threadIdx.x + u * kThreads;
+        hs[u] = 0;
+        if (q < nq) {
+            g4[u] = G4[q];
+            b4[u] = B4[q];
+            c4[u] = C4[q];
+            x4[u] = A4[q];
+            hs[u] = a.hot_slot ? __ldg(a.hot_slot + ((q << 2) >> log2Rp)) : -1;
         }
     }
 #pragma unroll
-    for (int u = 0; u < kPostUnroll; ++u)
-        if (hs[u] >= 0) fold_quad(a, hs[u], col[u], g4[u]);
-    float4 b4[kPostUnroll], c4[kPostUnroll], x4[kPostUnroll];
-#pragma unroll
-    for (int u = 0; u < kPostUnroll; ++u)
-        if (q[u] < nq && col[u] < a.R) {
-            b4[u] = reinterpret_cast<const float4 *>(a.B)[q[u]];
-            c4[u] = reinterpret_cast<const float4 *>(a.C)[q[u]];
-            x4[u] = reinterpret_cast<const float4 *>(a.A)[q[u]];
-        }
-#pragma unroll
-    for (int u = 0; u < kPostUnroll; ++u)
-        if (q[u] < nq && col[u] < a.R) adam_quad(a, q[u], col[u], g4[u], b4[u], c4[u], x4[u], k);
+    for (int u = 0; u < kPostUnroll; ++u) {
+        const int64_t q = (int64_t)ch.y + threadIdx.x + u * kThreads;
+        const int col = (int)((q << 2) & (a.Rp - 1));
+        if (hs[u] >= 0 || col >= a.R) continue;  // beyond the client, or a hot quad (the hot chunks take it)
+        adam_quad(a, q, col, g4[u], b4[u], c4[u], x4[u], k);
+    }
 }
 
 // Gradients cleared before the fused pass (grid.y = client).
@@ -739,6 +752,9 @@ gcp_status gcp_batch_create(int32_t nclients, gcp_ctx *const *clients, const int
     for (int i = 0; i < nclients; ++i) chunks.push_back(make_int2(i, -1));
     for (int i = 0; i < nclients; ++i)
         for (int64_t q0 = 0; q0 < aux[i].nparam / 4; q0 += gcpb::kPostQuads) chunks.push_back(make_int2(i, (int)q0));
+    for (int i = 0; i < nclients; ++i)  // hot chunks: code -2 - (first hot quad)
+        for (int64_t h = 0; h < (int64_t)aux[i].Htot * (aux[i].Rp / 4); h += gcpb::kHotQuadsPerChunk)
+            chunks.push_back(make_int2(i, (int)(-2 - h)));
     b->nchunks = (int)chunks.size();
     cudaError_t e;
     int prev = -1;

@@ -62,7 +62,8 @@ struct PostSpec {
     int Rp, R, Htot;
     float *G, *Grep, *A, *B, *C;
     void *Abf;
-    const int *hot_slot;
+    const int *hot_slot;            // row -> replica slot, or -1
+    const int *hot_row;             // replica slot -> row
     float lr, beta1, beta2, c1inv, c2inv, eps, lower;
     const double *partials;
     int nblocks;

@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 
 #include "gcp_device.cuh"
+#include "gcp_epilogue.cuh"
 #include "gcp_internal.h"
 
 using namespace gcpdev;
@@ -25,6 +26,7 @@ namespace gcpk {
 constexpr int kThreads = 256;
 
 static int elementwise_blocks(int64_t n);
+static int num_sms();
 
 struct RowOffsets {
     int64_t off[GCP_MAX_NDIM];
@@ -495,14 +497,30 @@ __global__ void k_adam(int64_t n, int Rp, int R, float *__restrict__ A, float *_
     }
 }
 
-// One training step's epilogue after the fused pass, in one launch: the last
-// block finishes the FP64 loss from the block partials (fixed order), while
-// the others take every element of the flat parameter vector: its gradient
-// (adding the replicas of a hot row and clearing them), Algorithm 1, and G
-// cleared for the next step.
-constexpr int kPostFold = 16;  // replica loads of a hot element in flight at a time
+// One training step's epilogue after the fused pass, in one launch, on
+// 16-byte quads of the flat parameter vector (Rp is a power of two and a
+// multiple of 4, so a quad lies in one row):
+//  - the last block finishes the FP64 loss from the block partials (fixed
+//    order);
+//  - the first `ncold` blocks stream the quads of rows without replicas:
+//    each thread takes kPostUnroll quads per iteration and issues all of
+//    their loads (gradient, moments, factor, replica slot) before using any,
+//    then applies Algorithm 1 and clears G for the next step;
+//  - the blocks between take the quads of hot rows, one per group of
+//    kHotLanes lanes: the group loads the quad's kReplicas replica quads at
+//    once (gcpe::hot_quad_sum, which also clears them), and its first lane
+//    adds them to the gradient quad and applies Algorithm 1.
+// The streaming blocks run at the copy rate on models larger than L2; the
+// hot quads cost one memory round trip each instead of one per group of
+// replica loads.
+// Quads per streaming thread and iteration.  One quad per thread at full
+// occupancy streamed the HBM-resident epilogue (121.6M parameters) at
+// 6.0 TB/s; two or four per thread, with fewer resident warps, at 3.6 and
+// 4.1 TB/s.
+constexpr int kPostUnroll = 1;
+static_assert(kReplicas % gcpe::kHotLanes == 0, "hot-quad replicas split evenly over the folding lanes");
 
-__global__ void __launch_bounds__(kThreads) k_post_step(PostSpec P) {
+__global__ void __launch_bounds__(kThreads) k_post_step(PostSpec P, int ncold) {
     if (blockIdx.x == gridDim.x - 1) {  // the last block only finishes the loss
         __shared__ double sh[3][kThreads];
         double t[3] = {0.0, 0.0, 0.0};
@@ -523,42 +541,91 @@ __global__ void __launch_bounds__(kThreads) k_post_step(PostSpec P) {
         }
         return;
     }
-    const int64_t plane = (int64_t)P.Htot * P.Rp;
-    const int log2Rp = __ffs(P.Rp) - 1;  // Rp is a power of two
-    const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < P.n; e += stride) {
-        const int row = (int)(e >> log2Rp), col = (int)(e & (P.Rp - 1));
-        // the gradient, the moments, the factor and the replica slot are
-        // independent loads, issued together
-        float g = P.G[e];
-        const float b0 = P.B[e], c0 = P.C[e], a0 = P.A[e];
-        const int hs = P.hot_slot ? __ldg(P.hot_slot + row) : -1;
-        if (hs >= 0) {  // replicas added in replica order, kPostFold loads in flight at a time, then cleared
-            const int64_t o = (int64_t)hs * P.Rp + col;
-            for (int r0 = 0; r0 < kReplicas; r0 += kPostFold) {
-                float v[kPostFold];
+    float4 *__restrict__ G4 = reinterpret_cast<float4 *>(P.G);
+    float4 *__restrict__ A4 = reinterpret_cast<float4 *>(P.A);
+    float4 *__restrict__ B4 = reinterpret_cast<float4 *>(P.B);
+    float4 *__restrict__ C4 = reinterpret_cast<float4 *>(P.C);
+    uint2 *__restrict__ Abf = static_cast<uint2 *>(P.Abf);
+    const int log2Rp = __ffs(P.Rp) - 1;
+    if ((int)blockIdx.x >= ncold) {  // hot quads, one per group of kHotLanes lanes
+        const int log2Q = log2Rp - 2;  // quads per row = Rp / 4
+        const int64_t hq = (int64_t)(blockIdx.x - ncold) * (kThreads / gcpe::kHotLanes) +
+                           (threadIdx.x / gcpe::kHotLanes);
+        if (hq >= ((int64_t)P.Htot << log2Q)) return;  // the whole group leaves together
+        const int slot = (int)(hq >> log2Q), cq = (int)(hq & ((1 << log2Q) - 1));
+        const int64_t q = ((int64_t)__ldg(P.hot_row + slot) << log2Q) + cq;
+        const bool lead = (threadIdx.x & (gcpe::kHotLanes - 1)) == 0;
+        float4 g, a, b, c;
+        if (lead) {
+            g = G4[q];
+            a = A4[q];
+            b = B4[q];
+            c = C4[q];
+        }
+        const float4 t = gcpe::hot_quad_sum<kReplicas>(reinterpret_cast<float4 *>(P.Grep),
+                                                       ((int64_t)P.Htot * P.Rp) >> 2, hq, gcpe::hot_group_mask());
+        if (!lead) return;
+        g.x += t.x;
+        g.y += t.y;
+        g.z += t.z;
+        g.w += t.w;
+        G4[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const int col = cq << 2;
+        if (col >= P.R) return;  // a quad of padding columns
+        adam_quad(a, b, c, g, col, P.R, P.lr, P.beta1, P.beta2, P.c1inv, P.c2inv, P.eps, P.lower,
+                  Abf ? Abf + q : nullptr);
+        A4[q] = a;
+        B4[q] = b;
+        C4[q] = c;
+        return;
+    }
+    // block tiles of kThreads * kPostUnroll consecutive quads; thread t takes
+    // quads t, t + kThreads, ... of its block's tile
+    const int64_t nq = P.n >> 2;
+    constexpr int64_t kTile = (int64_t)kThreads * kPostUnroll;
+    for (int64_t q0 = (int64_t)blockIdx.x * kTile + threadIdx.x; q0 < nq; q0 += (int64_t)ncold * kTile) {
+        float4 g[kPostUnroll], a[kPostUnroll], b[kPostUnroll], c[kPostUnroll];
+        int hs[kPostUnroll];
 #pragma unroll
-                for (int r = 0; r < kPostFold; ++r) v[r] = P.Grep[(r0 + r) * plane + o];
-#pragma unroll
-                for (int r = 0; r < kPostFold; ++r) g += v[r];
-#pragma unroll
-                for (int r = 0; r < kPostFold; ++r) P.Grep[(r0 + r) * plane + o] = 0.0f;
+        for (int u = 0; u < kPostUnroll; ++u) {
+            const int64_t q = q0 + u * kThreads;
+            hs[u] = -1;
+            if (q < nq) {
+                g[u] = G4[q];
+                a[u] = A4[q];
+                b[u] = B4[q];
+                c[u] = C4[q];
+                if (P.hot_slot) hs[u] = __ldg(P.hot_slot + ((q << 2) >> log2Rp));
             }
         }
-        P.G[e] = 0.0f;
-        if (col >= P.R) continue;
-        const float b = P.beta1 * b0 + (1.0f - P.beta1) * g;
-        const float c = P.beta2 * c0 + (1.0f - P.beta2) * g * g;
-        P.B[e] = b;
-        P.C[e] = c;
-        const float a = fmaxf(a0 - P.lr * ((b * P.c1inv) / sqrtf(c * P.c2inv + P.eps)), P.lower);
-        P.A[e] = a;
-        if (P.Abf) static_cast<__nv_bfloat16 *>(P.Abf)[e] = __float2bfloat16_rn(a);
+#pragma unroll
+        for (int u = 0; u < kPostUnroll; ++u) {
+            const int64_t q = q0 + u * kThreads;
+            if (q >= nq || hs[u] >= 0) continue;  // hot quads belong to the hot blocks
+            G4[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            const int col = (int)((q << 2) & (P.Rp - 1));
+            if (col >= P.R) continue;  // a quad of padding columns: nothing to update
+            adam_quad(a[u], b[u], c[u], g[u], col, P.R, P.lr, P.beta1, P.beta2, P.c1inv, P.c2inv, P.eps, P.lower,
+                      Abf ? Abf + q : nullptr);
+            A4[q] = a[u];
+            B4[q] = b[u];
+            C4[q] = c[u];
+        }
     }
 }
 
 cudaError_t launch_post_step(const PostSpec &p, cudaStream_t st) {
-    k_post_step<<<elementwise_blocks(p.n) + 1, kThreads, 0, st>>>(p);  // + the loss block
+    static int resident = 0;  // streaming blocks that fit on the GPU at once
+    if (!resident) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_post_step, kThreads, 0);
+        resident = (per_sm < 1 ? 1 : per_sm) * num_sms();
+    }
+    const int64_t want = ((p.n >> 2) + (int64_t)kThreads * kPostUnroll - 1) / ((int64_t)kThreads * kPostUnroll);
+    const int ncold = (int)(want < 1 ? 1 : (want > resident ? resident : want));
+    const int64_t hot_quads = (int64_t)p.Htot * (p.Rp >> 2);
+    const int nhot = (int)((hot_quads + kThreads / gcpe::kHotLanes - 1) / (kThreads / gcpe::kHotLanes));
+    k_post_step<<<ncold + nhot + 1, kThreads, 0, st>>>(p, ncold);  // + the loss block
     return cudaGetLastError();
 }
 
