@@ -61,14 +61,17 @@ def algorithmic_bytes_per_sample(d, R, nnz, M, elt_bytes):
     return 0.5 * (4 * (d + 1) + rows) + 0.5 * (32 * attempts + rows)
 
 
-def compulsory_bytes_per_sample(d, R, nnz, M, rows, elt_bytes=4):
-    """HBM bytes a sample cannot avoid when the model stays in L2: one 32-byte
-    sector for a nonzero's record, one 32-byte bucket sector per rejection
-    attempt for a zero, plus the model (factors read, gradient read and
+def compulsory_bytes_per_sample(d, R, nnz, M, rows, access_bytes=128, elt_bytes=4):
+    """HBM bytes a sample cannot avoid when the model stays in L2: one
+    random access for a nonzero's record, one per rejection attempt for a
+    zero's hash bucket, plus the model (factors read, gradient read and
     written once per step: rows x R x 3 x 4 B) spread over the step's 2^21
-    samples."""
+    samples.  On this GPU a random access that misses L2 moves a whole
+    128-byte DRAM line whatever its width (`bench.py --only dramprobe`
+    under ncu: 124 B of DRAM reads per random 16-128 B access);
+    access_bytes=32 gives the 32-byte-sector reading instead."""
     attempts = 1.0 / (1.0 - nnz / M)
-    return 0.5 * 32 + 0.5 * 32 * attempts + rows * R * (elt_bytes + 8) / float(1 << 21)
+    return 0.5 * access_bytes + 0.5 * access_bytes * attempts + rows * R * (elt_bytes + 8) / float(1 << 21)
 
 
 # the fused pass's part of gcp_kernels.cu ends where the replica fold begins
@@ -585,6 +588,26 @@ def l2_ceiling(gcp, torch, stream, d, Rp, S, reps=10, rows=1 << 15):
     return out
 
 
+def dram_access_cost(gcp, torch, stream, ops=1 << 21, gib=2):
+    """Random row accesses that miss L2: gcp_probe_l2's row operations, one
+    uniformly random row per op, on a 2 GiB buffer (16 times L2).  Rows of
+    16, 32, 64 and 128 B are read and rows of 64 and 128 B reduced, 2^21
+    ops each, one launch per kind; under ncu (dram__bytes_read.sum,
+    dram__bytes_write.sum) the launches give the DRAM bytes that one random
+    access of each width costs.  CUDA-event times are reported beside."""
+    buf = torch.zeros(gib << 28, dtype=torch.float32, device="cuda")
+    out = {"buffer_gib": gib, "ops": ops}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for kind, rf in (("load", 4), ("load", 8), ("load", 16), ("load", 32), ("red", 16), ("red", 32)):
+        e0.record(stream)
+        gcp.gcp_probe_l2(kind, buf, rf, 1, ops, stream)
+        e1.record(stream)
+        e1.synchronize()
+        out[f"{kind}_{4 * rf}B_ms"] = e0.elapsed_time(e1)
+    del buf
+    return out
+
+
 def combine_ranks(seconds, units_per_rank, world, dist=None, device="cpu"):
     """Whole-job throughput of N independent replicas: every rank processed
     units_per_rank units; the job took as long as its slowest rank (max over
@@ -755,7 +778,7 @@ def run_ours(args):
     if args.only:  # profiling captures: one variant alone
         stream = torch.cuda.current_stream()
         fn = {"batched": batched_variant, "hbm": hbm_resident_variant, "nonfused": fused_vs_nonfused_variant,
-              "bernoulli": bernoulli_variant, "autograd": autograd_variant}.get(args.only)
+              "bernoulli": bernoulli_variant, "autograd": autograd_variant, "dramprobe": dram_access_cost}.get(args.only)
         if args.only == "l2probe":
             res = l2_ceiling(gcp, torch, stream, 4, 32, 1 << 21)
         else:
@@ -876,6 +899,8 @@ def run_ours(args):
     dram = measured_traffic()
     compulsory = compulsory_bytes_per_sample(4, R, len(w["vals"]), float(np.prod(dims, dtype=np.float64)),
                                              sum(dims))
+    sector_bytes = compulsory_bytes_per_sample(4, R, len(w["vals"]), float(np.prod(dims, dtype=np.float64)),
+                                               sum(dims), access_bytes=32)
     roofline = {"bound": "l2", "achieved": achieved, "peak": ceil["both"]["gbs"], "unit": "GB/s",
                 "frac": achieved / ceil["both"]["gbs"], "traffic": dram, "kernel": "k_fused<4,float,4>",
                 "kernel_ms_per_launch": kernel_avg_s * 1e3,
@@ -894,7 +919,10 @@ def run_ours(args):
                         "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                         "dram_bytes_per_sample": dram / S if dram else None,
                         "compulsory_bytes_per_sample": compulsory,
-                        "dram_over_compulsory": dram / S / compulsory if dram else None},
+                        "compulsory_note": "one 128-B DRAM line per random record or bucket access (measured "
+                                           "granularity of this GPU) + the model amortised over the step",
+                        "dram_over_compulsory": dram / S / compulsory if dram else None,
+                        "sector_bytes_per_sample": sector_bytes},
                 # the scope table's logical bytes (record or bucket, gathers,
                 # reductions) over the kernel time: most are served by L2, so
                 # this is not an HBM fraction
@@ -939,7 +967,7 @@ def main():
     ap.add_argument("--kernel-only", action="store_true", help="time the step loop only (profiling)")
     ap.add_argument("--no-variants", action="store_true", help="skip the batched and HBM-resident variants")
     ap.add_argument("--only", default=None,
-                    choices=["batched", "hbm", "nonfused", "bernoulli", "autograd", "l2probe"],
+                    choices=["batched", "hbm", "nonfused", "bernoulli", "autograd", "l2probe", "dramprobe"],
                     help="run one variant alone (profiling captures)")
     ap.add_argument("--dtype", default="fp32", choices=["fp32", "bf16"], help="factor storage for --kernel-only")
     args = ap.parse_args()

@@ -231,6 +231,20 @@ gcp_status gcp_grad(gcp_ctx *ctx, uint64_t iter, int64_t p, int64_t q, float *G_
 gcp_status gcp_grad_async(gcp_ctx *ctx, uint64_t iter, int64_t p, int64_t q, const float *dscale,
                           float *G_out, double *dloss_out);
 
+/* Stage every mode's factor matrix and run the fused pass, in one call (the
+ * autograd binding's forward evaluation; the paper has no counterpart).
+ * A_modes (host array of ndim pointers) points to the per-mode matrices,
+ * I_k x R FP32 row-major, each contiguous, in device or managed memory
+ * (GCP_ERR_ARG otherwise); they are copied into the context by one kernel
+ * (with the BF16 copy refreshed), asynchronously on the context's stream,
+ * so they must stay valid until the stream has consumed them.  Then, as
+ * gcp_grad_async with dscale NULL: the sampled loss of iteration `iter` to
+ * dloss_out[0] (device, nullable) and, if G_out (device, flat FP32) is not
+ * NULL, the sampled gradient there; with G_out NULL only the loss is formed
+ * (as gcp_loss_async).  Asynchronous. */
+gcp_status gcp_grad_factors_async(gcp_ctx *ctx, const float *const *A_modes, uint64_t iter, int64_t p, int64_t q,
+                                  float *G_out, double *dloss_out);
+
 /* y[i] = (float)dscale[0] * x[i] for i < n, on the context's stream.
  * dscale (one FP64 value, as the FP64 loss's incoming gradient is), x and y
  * are device pointers (y may equal x); nothing is allocated.  The paper has

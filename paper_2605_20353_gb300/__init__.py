@@ -80,6 +80,7 @@ SIGNATURES = {
     "gcp_set_factors": (_i32, [_vp, _vp]),
     "gcp_set_factor": (_i32, [_vp, _i32, _vp]),
     "gcp_set_factor_list": (_i32, [_vp, _vp]),
+    "gcp_grad_factors_async": (_i32, [_vp, _vp, _u64, _i64, _i64, _vp, _vp]),
     "gcp_get_factors": (_i32, [_vp, _vp]),
     "gcp_reset_adam": (_i32, [_vp]),
     "gcp_sample": (_i32, [_vp, _u64, _i64, _i64, _vp, _vp, _vp]),

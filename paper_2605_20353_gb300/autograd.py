@@ -22,22 +22,37 @@ import torch
 from . import GcpContext, _check, load
 
 
-def _stage_factors(ctx: GcpContext, factors):
-    """Copy the factor tensors into the context in one call (asynchronous,
-    on its stream); returns the FP32 contiguous tensors, which must stay
-    alive until the copies have run."""
+def _factor_ptrs(ctx: GcpContext, factors):
+    """(pointer array, FP32 contiguous CUDA tensors) of the factor tensors;
+    the tensors must stay alive until the stream has consumed them."""
     staged = []
     ptrs = (ctypes.c_void_p * len(factors))()
     for k, a in enumerate(factors):
         t = a.detach()
-        if t.dtype != torch.float32 or not t.is_contiguous():
-            t = t.to(torch.float32).contiguous()
-        if t.shape[0] != ctx.dims[k] or t.shape[1] != ctx.rank or t.dim() != 2:
+        if t.dtype != torch.float32 or not t.is_contiguous() or not t.is_cuda:
+            t = t.to(device="cuda", dtype=torch.float32).contiguous()
+        if t.dim() != 2 or t.shape[0] != ctx.dims[k] or t.shape[1] != ctx.rank:
             raise ValueError(f"factor {k} has shape {tuple(t.shape)}, expected {(ctx.dims[k], ctx.rank)}")
         ptrs[k] = t.data_ptr()
         staged.append(t)
-    _check(load().gcp_set_factor_list(ctx.handle, ptrs), ctx.handle)
+    return ptrs, staged
+
+
+def _stage_and_run(ctx: GcpContext, factors, iteration, p, q, G, loss):
+    """One C call: stage the factors into the context and run the fused pass
+    (gradient into G when G is not None, loss into loss[0])."""
+    ptrs, staged = _factor_ptrs(ctx, factors)
+    _check(load().gcp_grad_factors_async(ctx.handle, ptrs, iteration, p, q, G.data_ptr() if G is not None else None,
+                                         loss.data_ptr()), ctx.handle)
     return staged
+
+
+def _grads_of(ctx: GcpContext, G, needs):
+    grads, o = [], 0
+    for k, I in enumerate(ctx.dims):
+        grads.append(G[o:o + I * ctx.rank].view(I, ctx.rank) if needs[4 + k] else None)
+        o += I * ctx.rank
+    return grads
 
 
 class GcpSampledLoss(torch.autograd.Function):
@@ -49,32 +64,27 @@ class GcpSampledLoss(torch.autograd.Function):
 
     @staticmethod
     def forward(fctx, ctx: GcpContext, iteration: int, p: int, q: int, *factors):
-        staged = _stage_factors(ctx, factors)
         dev = factors[0].device
         loss = torch.empty(1, dtype=torch.float64, device=dev)
         fctx.gcp = ctx
         fctx.G = None
         if any(fctx.needs_input_grad[4:]):
             fctx.G = torch.empty(ctx.num_params, dtype=torch.float32, device=dev)
-            ctx.grad_async(iteration, p, q, G_out=fctx.G, dloss=loss)
-        else:
-            ctx.loss_async(iteration, p, q, loss)
-        fctx.staged = staged  # alive until the stream has consumed them
+        fctx.staged = _stage_and_run(ctx, factors, iteration, p, q, fctx.G, loss)  # alive until consumed
         return loss.reshape(())
 
     @staticmethod
     def backward(fctx, grad_out):
         ctx: GcpContext = fctx.gcp
-        scale = grad_out.detach().to(torch.float64).reshape(1).contiguous()  # no copy for an FP64 seed
+        scale = grad_out.detach()
+        if scale.dtype != torch.float64:
+            scale = scale.to(torch.float64)
+        scale = scale.reshape(1).contiguous()  # a view for the usual FP64 seed
         G = torch.empty_like(fctx.G)
-        ctx.scale_async(scale, fctx.G, G)
-        grads, o = [], 0
-        for k, I in enumerate(ctx.dims):
-            g = G[o:o + I * ctx.rank].view(I, ctx.rank)
-            grads.append(g if fctx.needs_input_grad[4 + k] else None)
-            o += I * ctx.rank
+        _check(load().gcp_scale_async(ctx.handle, scale.data_ptr(), fctx.G.data_ptr(), G.data_ptr(), G.numel()),
+               ctx.handle)
         fctx.staged = fctx.staged + [scale, fctx.G]  # alive until the stream has consumed them
-        return (None, None, None, None, *grads)
+        return (None, None, None, None, *_grads_of(ctx, G, fctx.needs_input_grad))
 
 
 class GcpSampledLossAdjoint(torch.autograd.Function):
@@ -86,9 +96,8 @@ class GcpSampledLossAdjoint(torch.autograd.Function):
 
     @staticmethod
     def forward(fctx, ctx: GcpContext, iteration: int, p: int, q: int, *factors):
-        staged = _stage_factors(ctx, factors)
         loss = torch.empty(1, dtype=torch.float64, device=factors[0].device)
-        ctx.loss_async(iteration, p, q, loss)
+        staged = _stage_and_run(ctx, factors, iteration, p, q, None, loss)
         fctx.gcp, fctx.args, fctx.staged = ctx, (iteration, p, q), staged
         fctx.save_for_backward(*[f.detach() for f in factors])
         return loss.reshape(())
@@ -97,17 +106,13 @@ class GcpSampledLossAdjoint(torch.autograd.Function):
     def backward(fctx, grad_out):
         ctx: GcpContext = fctx.gcp
         factors = fctx.saved_tensors
-        staged = _stage_factors(ctx, factors)  # the factors as of the forward pass
+        ptrs, staged = _factor_ptrs(ctx, factors)  # the factors as of the forward pass
+        _check(load().gcp_set_factor_list(ctx.handle, ptrs), ctx.handle)
         seed = grad_out.detach().to(torch.float32).reshape(1).contiguous()
         G = torch.empty(ctx.num_params, dtype=torch.float32, device=seed.device)
         ctx.grad_async(*fctx.args, dscale=seed, G_out=G)
-        grads, o = [], 0
-        for k, I in enumerate(ctx.dims):
-            g = G[o:o + I * ctx.rank].view(I, ctx.rank)
-            grads.append(g if fctx.needs_input_grad[4 + k] else None)
-            o += I * ctx.rank
         fctx.staged = fctx.staged + staged + [seed]  # alive until the stream has consumed them
-        return (None, None, None, None, *grads)
+        return (None, None, None, None, *_grads_of(ctx, G, fctx.needs_input_grad))
 
 
 def sampled_loss(ctx: GcpContext, iteration: int, p: int, q: int, factors, grad_in_forward: bool = True):

@@ -1,6 +1,7 @@
 // gcp_api.cu -- the C ABI of include/gcp.h: context set-up, argument checks,
 // the stratified weights of Sec. 3.1.1, kernel launches and the GCP-Adam
 // epoch loop (Algorithm 2 on one GPU).
+#include <cuda_bf16.h>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -408,6 +409,27 @@ __global__ void k_check_dense(const float *X, int64_t n, int loss, int *status) 
     if (bad) atomicOr(status, bad);
 }
 
+// Every mode's factor matrix (src.A[k], I_k x R row-major, device memory)
+// copied into the context's padded flat layout in one launch; padding
+// columns are written as zero and the BF16 copy, if any, is refreshed.
+struct FactorSrc {
+    const float *A[GCP_MAX_NDIM];
+    int64_t rowoff[GCP_MAX_NDIM + 1];  // first row of each mode, then the total
+};
+
+__global__ void k_stage_factors(FactorSrc src, int d, int R, int log2Rp, int64_t n, float *__restrict__ A,
+                                __nv_bfloat16 *__restrict__ Abf) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e >> log2Rp;
+        const int col = (int)(e & ((1 << log2Rp) - 1));
+        int k = 0;
+        while (k + 1 < d && row >= src.rowoff[k + 1]) ++k;
+        const float v = col < R ? __ldg(src.A[k] + (row - src.rowoff[k]) * R + col) : 0.0f;
+        A[e] = v;
+        if (Abf) Abf[e] = __float2bfloat16_rn(v);
+    }
+}
+
 // y = s[0] * x elementwise (x and y may be the same array); s is FP64,
 // rounded once to FP32.
 __global__ void k_scale(const double *s, const float *x, float *y, int64_t n) {
@@ -770,6 +792,39 @@ gcp_status gcp_grad_async(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, const
     if (s) return s;
     s = copy_grad_out(c, G_out);
     if (s) return s;
+    if (dloss_out)
+        GCP_CUDA(c, cudaMemcpyAsync(dloss_out, c->dloss, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    return GCP_OK;
+}
+
+gcp_status gcp_grad_factors_async(gcp_ctx *c, const float *const *A_modes, uint64_t iter, int64_t p, int64_t q,
+                                  float *G_out, double *dloss_out) {
+    if (!c || !A_modes) return fail(c, GCP_ERR_ARG, "NULL argument");
+    FactorSrc src{};
+    for (int k = 0; k < c->d; ++k) {
+        if (!A_modes[k]) return fail(c, GCP_ERR_ARG, "NULL factor pointer");
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, A_modes[k]) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();  // a host pointer is an argument error, not a sticky CUDA error
+            return fail(c, GCP_ERR_ARG, "factor matrices must be device or managed memory");
+        }
+        src.A[k] = A_modes[k];
+        src.rowoff[k] = c->rowoff[k];
+    }
+    src.rowoff[c->d] = c->total_rows;
+    DeviceGuard g(c->device);
+    gcp_status s = check_counts(c, p, q);
+    if (s) return s;
+    const int64_t n = c->total_rows * c->Rp;
+    int log2Rp = 0;
+    while ((1 << log2Rp) < c->Rp) ++log2Rp;
+    const int64_t want = (n + 255) / 256;
+    k_stage_factors<<<(unsigned)(want < 8192 ? want : 8192), 256, 0, c->st>>>(
+        src, c->d, c->R, log2Rp, n, c->A, static_cast<__nv_bfloat16 *>(c->Abf));
+    GCP_CUDA(c, cudaGetLastError());
+    if ((s = run_fused(c, iter, p, q, G_out != nullptr, nullptr))) return s;
+    if ((s = copy_grad_out(c, G_out))) return s;
     if (dloss_out)
         GCP_CUDA(c, cudaMemcpyAsync(dloss_out, c->dloss, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     return GCP_OK;

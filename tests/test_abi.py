@@ -100,6 +100,7 @@ def test_factor_list_and_scale_reject_null_arguments_on_the_host(lib_path):
 
     lib = gcp.load()
     assert lib.gcp_set_factor_list(None, None) == 1
+    assert lib.gcp_grad_factors_async(None, None, 0, 1, 1, None, None) == 1
     assert lib.gcp_scale_async(None, None, None, None, 4) == 1
     assert lib.gcp_grad_norm(None, None) == 1
 

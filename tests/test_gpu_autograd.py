@@ -154,3 +154,40 @@ def test_autograd_adjoint_in_backward(env, scale):
     for n, (a, g) in enumerate(zip(A, Go)):
         assert rel_err(a.grad.cpu().numpy(), scale * g) <= TOL, n
     ctx.close()
+
+
+def test_stage_and_gradient_call_matches_separate_calls_and_rejects_host_memory(env):
+    """gcp_grad_factors_async (stage every factor matrix with one kernel, then
+    the fused pass) gives the loss and gradient of gcp_set_factor_list +
+    gcp_grad_async bit for bit, pads the rank with zeros, and rejects factor
+    matrices in host memory with GCP_ERR_ARG."""
+    import ctypes
+
+    gcp, torch, _ = env
+    dims, R = [30, 20, 10], 6  # rows padded to 8 columns
+    coords, vals = synth.uniform_sparse(dims, 500, 4401, lam=2.0)
+    fac = [torch.tensor(a, device="cuda") for a in synth.factors_uniform(dims, R, 4402, lo=0.1, hi=1.0)]
+    lib = gcp.load()
+    a = gcp.gcp_create(dims, coords, vals, R, "poisson", seed=4403)
+    b = gcp.gcp_create(dims, coords, vals, R, "poisson", seed=4403)
+    b.set_factors([f.cpu().numpy() for f in fac])
+    ptrs = (ctypes.c_void_p * 3)(*[f.data_ptr() for f in fac])
+    Ga = torch.zeros(a.num_params, device="cuda")
+    La = torch.zeros(1, dtype=torch.float64, device="cuda")
+    assert lib.gcp_grad_factors_async(a.handle, ptrs, 7, 300, 301, Ga.data_ptr(), La.data_ptr()) == 0
+    Gb = torch.zeros(b.num_params, device="cuda")
+    Lb = torch.zeros(1, dtype=torch.float64, device="cuda")
+    b.grad_async(7, 300, 301, G_out=Gb, dloss=Lb)
+    a.sync()
+    b.sync()
+    assert torch.equal(La, Lb)  # fixed-order loss reduction
+    assert torch.linalg.norm(Ga - Gb) <= 1e-6 * torch.linalg.norm(Gb)  # atomic summation order only
+    for x, y in zip(a.get_factors(), fac):
+        assert np.array_equal(x, y.cpu().numpy())
+    host = [f.cpu() for f in fac]
+    hptrs = (ctypes.c_void_p * 3)(*[h.data_ptr() for h in host])
+    assert lib.gcp_grad_factors_async(a.handle, hptrs, 7, 300, 301, Ga.data_ptr(), La.data_ptr()) == 1
+    assert b"device or managed" in lib.gcp_last_error(a.handle)
+    a.sync()  # the context stays usable
+    a.close()
+    b.close()
