@@ -373,8 +373,8 @@ def batched_variant(gcp, torch, stream, steps=20, with_oracle=True):
     clients = make("bf16")
     batch = gcp.GcpBatch(clients, P, P)
     best, times = autotune.tune_batch(batch, adam, tau=tau, reps=2)
-    res["autotune"] = {"best_lane_cols": best[0], "best_blocks": best[1],
-                       "ms_per_step": {f"{c}x{g}": t for (c, g), t in times.items()}}
+    res["autotune"] = {"best_lane_cols": best[0], "best_blocks": best[1], "best_samples_per_warp": best[2],
+                       "ms_per_step": {f"cols{c}_blocks{g}_tile{t}": ms for (c, g, t), ms in times.items()}}
     batch.local_steps(tau, adam, 0, 0)
     stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

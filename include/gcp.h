@@ -319,6 +319,16 @@ const char *gcp_batch_last_error(const gcp_batch *batch);
  * the graph at the next gcp_batch_local_steps. */
 gcp_status gcp_batch_tune(gcp_batch *batch, int32_t lane_cols, int32_t blocks);
 
+/* Tuning knob of the multi-client fused kernel: samples per warp tile (16,
+ * 32 or 64; 0 = 32).  A warp stages a tile's samples (one, or for 64 two,
+ * per lane; for 16 only half its lanes) and then evaluates them; smaller
+ * tiles spread a step over more warps, larger ones keep more sample loads
+ * in flight per warp.  The grid size follows the new tile size's occupancy
+ * unless gcp_batch_tune set it explicitly.  A change rebuilds the graph at
+ * the next gcp_batch_local_steps; results do not depend on the tile size
+ * beyond the FP32 summation order.  GCP_ERR_ARG for other sizes. */
+gcp_status gcp_batch_tune_tile(gcp_batch *batch, int32_t samples_per_warp);
+
 /* tau local steps of every client: step k (0-based) samples iteration
  * iter0 + k and applies Adam step t0 + k + 1 (Alg. 1) with prm.  Each client
  * ends with the same state as tau rounds of gcp_grad + gcp_adam_step on its

@@ -100,6 +100,7 @@ SIGNATURES = {
     "gcp_batch_destroy": (None, [_vp]),
     "gcp_batch_last_error": (ctypes.c_char_p, [_vp]),
     "gcp_batch_tune": (_i32, [_vp, _i32, _i32]),
+    "gcp_batch_tune_tile": (_i32, [_vp, _i32]),
     "gcp_batch_local_steps": (_i32, [_vp, _i32, ctypes.POINTER(gcp_adam_params), _u64, _i64]),
     "gcp_batch_losses": (_i32, [_vp, _vp]),
     "gcp_batch_server_init": (_i32, [_vp]),
@@ -427,7 +428,12 @@ class GcpBatch:
         if rc != GCP_OK:
             raise GcpError(rc, load().gcp_batch_last_error(self.handle).decode())
 
-    def tune(self, lane_cols=0, blocks=0):
+    def tune(self, lane_cols=0, blocks=0, samples_per_warp=None):
+        """Knobs of the multi-client fused kernel: factor columns per lane,
+        persistent grid size (0 = all resident blocks) and, if given,
+        samples per warp tile (16, 32 or 64)."""
+        if samples_per_warp is not None:
+            self._check(load().gcp_batch_tune_tile(self.handle, samples_per_warp))
         self._check(load().gcp_batch_tune(self.handle, lane_cols, blocks))
 
     def local_steps(self, tau, adam: AdamParams, iter0, t0):

@@ -46,8 +46,12 @@ struct ClientAux {
     int64_t nparam;  // total_rows * Rp
     int R, Rp;
     double w_nz, w_z;
-    int tile0, ntiles;
+    int tile0[3], ntiles[3];  // first tile and tile count at 16, 32 and 64 samples per tile
 };
+
+// Samples per warp tile: 16, 32 or 64 (index 0, 1, 2 of the per-size arrays).
+constexpr int kTileSizes[3] = {16, 32, 64};
+__host__ __device__ constexpr int tile_index(int ts) { return ts == 16 ? 0 : (ts == 32 ? 1 : 2); }
 
 template <int D>
 __device__ __forceinline__ void draw_tuple_b(const gcpk::SampleSpec &S, uint64_t stream, uint64_t j, uint64_t sub0,
@@ -82,19 +86,29 @@ __device__ __forceinline__ int client_of(const int *__restrict__ tile_start, int
 }
 
 // Multi-client fused sampled gradient.  Each client's FusedSpec (stored as
-// kSpecWords 16-byte words) gives its
-// tensor, model, gradient and weights; the iteration number is step[0].
-// Per tile, the FP32 loss sums (nonzero, zero) go to tile_loss[tile].
-template <int D, typename TF, int COLS>
+// kSpecWords 16-byte words) gives its tensor, model, gradient and weights;
+// the iteration number is step[0].  A tile holds TS consecutive samples of
+// one client (TS = 16, 32 or 64 samples per warp, a tuning knob): in phase
+// A, lane l stages the samples at positions l, l + 32, ... of the tile
+// (for TS = 16 lanes 16..31 stage nothing); in phase B the warp's groups
+// take the tile's samples in turn.  Per tile, the FP32 loss sums (nonzero,
+// zero) go to tile_loss[tile].
+template <int D, typename TF, int COLS, int TS>
 __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) k_batch_fused(const int4 *__restrict__ specs,
                                                          const int *__restrict__ tile_start, int nclients,
                                                          int total_tiles, int log2L, int Rp,
                                                          const uint64_t *__restrict__ step, float2 *tile_loss) {
     constexpr int SW = gcpk::rec_words_for(D);
     constexpr int NQ = COLS / 4;
-    __shared__ __align__(16) int32_t s_slot[2][kWarps][32][SW];
-    __shared__ __align__(16) uint64_t s_bkt[2][kWarps][32][4];
-    __shared__ __align__(16) int4 s_spec[2][kWarps][kSpecWords];
+    constexpr int SPL = TS >= 32 ? TS / 32 : 1;  // tile positions a lane stages
+    static_assert(TS == 16 || TS == 32 || TS == 64, "16, 32 or 64 samples per warp");
+    // staging in dynamic shared memory (batch_fused_smem bytes; 64-sample
+    // tiles need more than the 48 KB a kernel may declare statically)
+    extern __shared__ __align__(16) unsigned char smem[];
+    auto &s_slot = *reinterpret_cast<int32_t(*)[2][kWarps][TS][SW]>(smem);
+    auto &s_bkt = *reinterpret_cast<uint64_t(*)[2][kWarps][TS][4]>(smem + sizeof(int32_t) * 2 * kWarps * TS * SW);
+    auto &s_spec = *reinterpret_cast<int4(*)[2][kWarps][kSpecWords]>(
+        smem + sizeof(int32_t) * 2 * kWarps * TS * SW + sizeof(uint64_t) * 2 * kWarps * TS * 4);
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -128,48 +142,57 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
         return c;
     };
 
-    auto issue = [&](int tile, int st) -> uint64_t {
-        if (tile >= total_tiles) return kEmpty;
+    // A1: start the draws of this lane's positions of `tile` into stage st;
+    // key[j] = the stratified zero candidate of position lane + 32 j, else kEmpty.
+    auto issue = [&](int tile, int st, uint64_t (&key)[SPL]) {
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) key[j] = kEmpty;
+        if (tile >= total_tiles) return;
         const int c = stage_spec(tile, st);
         const gcpk::FusedSpec &P = spec_of(st);
         const int p = (int)P.s.p, S = (int)(P.s.p + P.s.q);
-        const int s = ((tile - __ldg(tile_start + c)) << 5) + lane;
-        int32_t *slot = s_slot[st][warp][lane];
-        if (s >= S) return kEmpty;
-        if (s < p) {
-            const U64x4 w = philox4x64_10((uint64_t)s, 0, P.s.iter, 0, P.s.seed, kStreamNonzero);
-            const int32_t *rec = P.s.rec + map_range(w.v[0], (uint64_t)P.s.nnz) * SW;
-#pragma unroll
-            for (int v = 0; v < SW / 4; ++v) cp_async16(slot + 4 * v, rec + 4 * v);
-            return kEmpty;
-        }
+        const int base = (tile - __ldg(tile_start + c)) * TS;
         const bool semi = P.s.sampling == GCP_SAMPLING_SEMI_STRATIFIED;
-        int32_t idx[D];
-        draw_tuple_b<D>(P.s, semi ? kStreamSemiZero : kStreamZero, (uint64_t)(s - p), 0, idx);
 #pragma unroll
-        for (int k = 0; k < D; ++k) slot[k] = idx[k];
-        slot[D] = 0;
-        if (semi) return kEmpty;
-        const uint64_t key = linear_b<D>(P.s, idx);
-        const uint64_t *b = P.s.hkeys + 4 * (mix64(key) & P.s.hbmask);
-        cp_async16(&s_bkt[st][warp][lane][0], b);
-        cp_async16(&s_bkt[st][warp][lane][2], b + 2);
-        return key;
+        for (int j = 0; j < SPL; ++j) {
+            const int pos = lane + 32 * j;
+            const int s = base + pos;
+            if (pos >= TS || s >= S) continue;
+            int32_t *slot = s_slot[st][warp][pos];
+            if (s < p) {
+                const U64x4 w = philox4x64_10((uint64_t)s, 0, P.s.iter, 0, P.s.seed, kStreamNonzero);
+                const int32_t *rec = P.s.rec + map_range(w.v[0], (uint64_t)P.s.nnz) * SW;
+#pragma unroll
+                for (int v = 0; v < SW / 4; ++v) cp_async16(slot + 4 * v, rec + 4 * v);
+                continue;
+            }
+            int32_t idx[D];
+            draw_tuple_b<D>(P.s, semi ? kStreamSemiZero : kStreamZero, (uint64_t)(s - p), 0, idx);
+#pragma unroll
+            for (int k = 0; k < D; ++k) slot[k] = idx[k];
+            slot[D] = 0;
+            if (semi) continue;
+            key[j] = linear_b<D>(P.s, idx);
+            const uint64_t *b = P.s.hkeys + 4 * (mix64(key[j]) & P.s.hbmask);
+            cp_async16(&s_bkt[st][warp][pos][0], b);
+            cp_async16(&s_bkt[st][warp][pos][2], b + 2);
+        }
     };
 
-    auto finish = [&](int tile, int st, uint64_t key) -> bool {
+    // A2: finish the draw of position pos of stage st; whether the sample exists.
+    auto finish = [&](int tile, int st, uint64_t key, int pos) -> bool {
         const gcpk::FusedSpec &P = spec_of(st);
         const int p = (int)P.s.p, S = (int)(P.s.p + P.s.q);
-        const int s = ((tile - __ldg(tile_start + cur_client[st])) << 5) + lane;
-        if (s >= S) return false;
+        const int s = (tile - __ldg(tile_start + cur_client[st])) * TS + pos;
+        if (pos >= TS || s >= S) return false;
         if (key == kEmpty) return true;
-        const ulonglong2 lo = *reinterpret_cast<const ulonglong2 *>(&s_bkt[st][warp][lane][0]);
-        const ulonglong2 hi = *reinterpret_cast<const ulonglong2 *>(&s_bkt[st][warp][lane][2]);
+        const ulonglong2 lo = *reinterpret_cast<const ulonglong2 *>(&s_bkt[st][warp][pos][0]);
+        const ulonglong2 hi = *reinterpret_cast<const ulonglong2 *>(&s_bkt[st][warp][pos][2]);
         int h = bucket_decide(lo, hi, key);
         if (h == 2)
             h = hash_contains_from(P.s.hkeys, P.s.hbmask, key, ((mix64(key) & P.s.hbmask) + 1) & P.s.hbmask, 1);
         if (h == 0) return true;
-        int32_t *slot = s_slot[st][warp][lane];
+        int32_t *slot = s_slot[st][warp][pos];
         const uint64_t j = (uint64_t)(s - p);
         for (int a = 1; h == 1 && a < P.s.max_attempts; ++a) {
             int32_t idx[D];
@@ -186,28 +209,33 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
     };
 
     int tile = warp0;
-    uint64_t key_next = issue(tile, 0);
+    uint64_t key_next[SPL];
+    issue(tile, 0, key_next);
     cp_async_commit();
     for (int st = 0; tile < total_tiles; tile += nwarps, st ^= 1) {
-        const uint64_t key = key_next;
+        uint64_t key[SPL];
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) key[j] = key_next[j];
         __syncwarp();
-        key_next = issue(tile + nwarps, st ^ 1);
+        issue(tile + nwarps, st ^ 1, key_next);
         cp_async_commit();
         cp_async_wait<1>();
-        const bool ok = finish(tile, st, key);
-        const unsigned okmask = __ballot_sync(0xFFFFFFFFu, ok);
+        uint64_t okmask = 0;  // bit pos: the sample at tile position pos exists
+#pragma unroll
+        for (int j = 0; j < SPL; ++j)
+            okmask |= (uint64_t)__ballot_sync(0xFFFFFFFFu, finish(tile, st, key[j], lane + 32 * j)) << (32 * j);
         __syncwarp();
 
         const gcpk::FusedSpec &P = spec_of(st);
         const TF *__restrict__ F = static_cast<const TF *>(P.F);
         const int p = (int)P.s.p;
-        const int tbase = (tile - __ldg(tile_start + cur_client[st])) << 5;
+        const int tbase = (tile - __ldg(tile_start + cur_client[st])) * TS;
         const bool semi = P.s.sampling == GCP_SAMPLING_SEMI_STRATIFIED;
         float *const grep = P.Grep ? P.Grep + (size_t)(warp0 & (gcpk::kReplicas - 1)) * P.Htot * Rp : nullptr;
         float tf_nz = 0.0f, tf_z = 0.0f;
-        for (int it = 0; it < L; ++it) {
+        for (int it = 0; it * ngrp < TS; ++it) {
             const int src = it * ngrp + grp;
-            if (!((okmask >> src) & 1u)) continue;
+            if (src >= TS || !((okmask >> src) & 1ull)) continue;  // uniform within the group
             const int32_t *slot = s_slot[st][warp][src];
             int32_t ii[D];
 #pragma unroll
@@ -308,13 +336,14 @@ __global__ void k_batch_set(uint64_t *step, double *adam, uint64_t iter0, uint64
 // Block-wide, fixed-order sum of client a's per-tile loss partials, weighted
 // (FP64).  Each thread adds its tiles t, t + kThreads, ... in that order; eight
 // loads are issued before their adds so the chain does not wait on each one.
-__device__ __forceinline__ void finish_client_loss(const ClientAux &a, const float2 *__restrict__ tile_loss,
+__device__ __forceinline__ void finish_client_loss(const ClientAux &a, int ti, const float2 *__restrict__ tile_loss,
                                                    double *out) {
     __shared__ double sh[2][kThreads];
     double nz = 0.0, z = 0.0;
-    const float2 *tl = tile_loss + a.tile0;
+    const float2 *tl = tile_loss + a.tile0[ti];
+    const int ntiles = a.ntiles[ti];
     int t = threadIdx.x;
-    for (; t + 7 * kThreads < a.ntiles; t += 8 * kThreads) {
+    for (; t + 7 * kThreads < ntiles; t += 8 * kThreads) {
         float2 v[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) v[r] = tl[t + r * kThreads];
@@ -324,7 +353,7 @@ __device__ __forceinline__ void finish_client_loss(const ClientAux &a, const flo
             z += v[r].y;
         }
     }
-    for (; t < a.ntiles; t += kThreads) {
+    for (; t < ntiles; t += kThreads) {
         const float2 v = tl[t];
         nz += v.x;
         z += v.y;
@@ -395,11 +424,11 @@ static_assert(gcpk::kReplicas % gcpe::kHotLanes == 0, "hot-quad replicas split e
 __global__ void __launch_bounds__(kThreads) k_batch_post(const ClientAux *__restrict__ aux,
                                                          const int2 *__restrict__ chunks,
                                                          const float2 *__restrict__ tile_loss, double *client_loss,
-                                                         const double *__restrict__ adam) {
+                                                         const double *__restrict__ adam, int ti) {
     const int2 ch = chunks[blockIdx.x];
     const ClientAux &a = aux[ch.x];
     if (ch.y == -1) {
-        finish_client_loss(a, tile_loss, client_loss + ch.x);
+        finish_client_loss(a, ti, tile_loss, client_loss + ch.x);
         return;
     }
     const AdamConsts k{(float)adam[0], (float)adam[1], (float)adam[2], (float)adam[3],
@@ -518,38 +547,80 @@ __global__ void k_fed_server(const ClientAux *__restrict__ aux, int n, float *U,
     }
 }
 
+// Dynamic shared memory of k_batch_fused<D, *, *, TS>: the double-buffered
+// sample slots and hash buckets of every warp, and the staged client specs.
+constexpr size_t batch_fused_smem(int d, int ts) {
+    return (size_t)2 * kWarps * ts * (gcpk::rec_words_for(d) * sizeof(int32_t) + 4 * sizeof(uint64_t)) +
+           (size_t)2 * kWarps * kSpecWords * sizeof(int4);
+}
+
+using FusedKernel = void (*)(const int4 *, const int *, int, int, int, int, const uint64_t *, float2 *);
+
+// The instantiation for (dtype, cols); with `allow`, its dynamic shared
+// memory limit is raised to what it needs (a host call made before any
+// launch or stream capture that uses it, on the batch's device).
+template <int D, typename TF, int COLS, int TS>
+cudaError_t fused_kernel_of(FusedKernel *k, bool allow) {
+    *k = k_batch_fused<D, TF, COLS, TS>;
+    if (!allow) return cudaSuccess;
+    return cudaFuncSetAttribute(k_batch_fused<D, TF, COLS, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)batch_fused_smem(D, TS));
+}
+
+template <int D, int TS>
+cudaError_t fused_kernel_ts(bool bf16, int cols, FusedKernel *k, bool allow) {
+    if (bf16)
+        return cols == 8 ? fused_kernel_of<D, __nv_bfloat16, 8, TS>(k, allow)
+                         : fused_kernel_of<D, __nv_bfloat16, 4, TS>(k, allow);
+    return cols == 8 ? fused_kernel_of<D, float, 8, TS>(k, allow) : fused_kernel_of<D, float, 4, TS>(k, allow);
+}
+
 template <int D>
-cudaError_t launch_fused_d(bool bf16, int cols, int blocks, const int4 *specs, const int *tile_start, int n,
-                           int total_tiles, int log2L, int Rp, const uint64_t *step, float2 *tile_loss,
-                           cudaStream_t st) {
-    if (bf16) {
-        if (cols == 8)
-            k_batch_fused<D, __nv_bfloat16, 8><<<blocks, kThreads, 0, st>>>(specs, tile_start, n, total_tiles, log2L,
-                                                                           Rp, step, tile_loss);
-        else
-            k_batch_fused<D, __nv_bfloat16, 4><<<blocks, kThreads, 0, st>>>(specs, tile_start, n, total_tiles, log2L,
-                                                                           Rp, step, tile_loss);
-    } else {
-        if (cols == 8)
-            k_batch_fused<D, float, 8><<<blocks, kThreads, 0, st>>>(specs, tile_start, n, total_tiles, log2L, Rp,
-                                                                   step, tile_loss);
-        else
-            k_batch_fused<D, float, 4><<<blocks, kThreads, 0, st>>>(specs, tile_start, n, total_tiles, log2L, Rp,
-                                                                   step, tile_loss);
-    }
+cudaError_t allow_fused_d(bool bf16, int cols, int ts) {
+    FusedKernel k = nullptr;
+    return ts == 16 ? fused_kernel_ts<D, 16>(bf16, cols, &k, true)
+                    : (ts == 64 ? fused_kernel_ts<D, 64>(bf16, cols, &k, true) : fused_kernel_ts<D, 32>(bf16, cols, &k, true));
+}
+
+template <int D, int TS>
+cudaError_t launch_fused_ts(bool bf16, int cols, int blocks, const int4 *specs, const int *tile_start, int n,
+                            int total_tiles, int log2L, int Rp, const uint64_t *step, float2 *tile_loss,
+                            cudaStream_t st) {
+    FusedKernel k = nullptr;
+    cudaError_t e = fused_kernel_ts<D, TS>(bf16, cols, &k, false);
+    if (e != cudaSuccess) return e;
+    k<<<blocks, kThreads, batch_fused_smem(D, TS), st>>>(specs, tile_start, n, total_tiles, log2L, Rp, step,
+                                                          tile_loss);
     return cudaGetLastError();
 }
 
 template <int D>
-int occupancy_d(bool bf16, int cols) {
+cudaError_t launch_fused_d(bool bf16, int cols, int ts, int blocks, const int4 *specs, const int *tile_start, int n,
+                           int total_tiles, int log2L, int Rp, const uint64_t *step, float2 *tile_loss,
+                           cudaStream_t st) {
+    if (ts == 16)
+        return launch_fused_ts<D, 16>(bf16, cols, blocks, specs, tile_start, n, total_tiles, log2L, Rp, step,
+                                      tile_loss, st);
+    if (ts == 64)
+        return launch_fused_ts<D, 64>(bf16, cols, blocks, specs, tile_start, n, total_tiles, log2L, Rp, step,
+                                      tile_loss, st);
+    return launch_fused_ts<D, 32>(bf16, cols, blocks, specs, tile_start, n, total_tiles, log2L, Rp, step, tile_loss,
+                                  st);
+}
+
+template <int D, int TS>
+int occupancy_ts(bool bf16, int cols) {
+    FusedKernel k = nullptr;
     int per_sm = 0;
-    if (bf16)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, cols == 8 ? k_batch_fused<D, __nv_bfloat16, 8> : k_batch_fused<D, __nv_bfloat16, 4>, kThreads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, cols == 8 ? k_batch_fused<D, float, 8> : k_batch_fused<D, float, 4>, kThreads, 0);
+    if (fused_kernel_ts<D, TS>(bf16, cols, &k, true) == cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, batch_fused_smem(D, TS));
     return per_sm < 1 ? 1 : per_sm;
+}
+
+template <int D>
+int occupancy_d(bool bf16, int cols, int ts) {
+    return ts == 16 ? occupancy_ts<D, 16>(bf16, cols) : (ts == 64 ? occupancy_ts<D, 64>(bf16, cols)
+                                                                  : occupancy_ts<D, 32>(bf16, cols));
 }
 
 }  // namespace gcpb
@@ -560,14 +631,15 @@ struct gcp_batch {
     bool bf16 = false;
     std::vector<gcp_ctx *> clients;
     std::vector<int64_t> p, q;
-    int total_tiles = 0;
-    int cols = 4, blocks = 0;        // tuning knobs: columns per lane, fused-kernel grid
+    int total_tiles[3] = {0, 0, 0};  // tiles of 16, 32 and 64 samples
+    int cols = 4, blocks = 0;        // tuning knobs: columns per lane, fused-kernel grid,
+    int ts = 32;                     //   samples per warp tile
     int4 *specs = nullptr;           // n x kSpecWords
-    int *tile_start = nullptr;       // n + 1
+    int *tile_start = nullptr;       // 3 x (n + 1): first tile of each client, per tile size
     int2 *chunks = nullptr;          // epilogue work list: {client, -1} loss, {client, first quad} Adam
     int nchunks = 0;
     gcpb::ClientAux *aux = nullptr;  // n
-    float2 *tile_loss = nullptr;     // total_tiles
+    float2 *tile_loss = nullptr;     // total_tiles of the smallest tile size
     double *client_loss = nullptr;   // n
     uint64_t *step = nullptr;        // [0] iteration of the next gradient, [1] Adam steps done
     double *adam = nullptr;          // lr, beta1, beta2, eps, lower, bias corrections, beta powers
@@ -576,7 +648,7 @@ struct gcp_batch {
     cudaStream_t st = nullptr, user_st = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t graph = nullptr;
-    int graph_tau = 0, graph_cols = 0, graph_blocks = 0;
+    int graph_tau = 0, graph_cols = 0, graph_blocks = 0, graph_ts = 0;
     float *U = nullptr, *Bs = nullptr, *Cs = nullptr;  // FedAdam server model and moments
     float *fed_c = nullptr, *h_fed_c = nullptr;        // server Adam constants (device, pinned)
     std::string err;
@@ -623,20 +695,33 @@ void batch_free(gcp_batch *b) {
     if (b->st) cudaStreamDestroy(b->st);
 }
 
-int default_blocks(const gcp_batch *b, int cols) {
+int default_blocks(const gcp_batch *b, int cols, int ts) {
     int per_sm = 1;
     switch (b->d) {
-    case 2: per_sm = gcpb::occupancy_d<2>(b->bf16, cols); break;
-    case 3: per_sm = gcpb::occupancy_d<3>(b->bf16, cols); break;
-    case 4: per_sm = gcpb::occupancy_d<4>(b->bf16, cols); break;
-    case 5: per_sm = gcpb::occupancy_d<5>(b->bf16, cols); break;
-    case 6: per_sm = gcpb::occupancy_d<6>(b->bf16, cols); break;
-    case 7: per_sm = gcpb::occupancy_d<7>(b->bf16, cols); break;
-    default: per_sm = gcpb::occupancy_d<8>(b->bf16, cols); break;
+    case 2: per_sm = gcpb::occupancy_d<2>(b->bf16, cols, ts); break;
+    case 3: per_sm = gcpb::occupancy_d<3>(b->bf16, cols, ts); break;
+    case 4: per_sm = gcpb::occupancy_d<4>(b->bf16, cols, ts); break;
+    case 5: per_sm = gcpb::occupancy_d<5>(b->bf16, cols, ts); break;
+    case 6: per_sm = gcpb::occupancy_d<6>(b->bf16, cols, ts); break;
+    case 7: per_sm = gcpb::occupancy_d<7>(b->bf16, cols, ts); break;
+    default: per_sm = gcpb::occupancy_d<8>(b->bf16, cols, ts); break;
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     return per_sm * sms;
+}
+
+cudaError_t allow_batch_fused(const gcp_batch *b) {
+    switch (b->d) {
+    case 2: return gcpb::allow_fused_d<2>(b->bf16, b->cols, b->ts);
+    case 3: return gcpb::allow_fused_d<3>(b->bf16, b->cols, b->ts);
+    case 4: return gcpb::allow_fused_d<4>(b->bf16, b->cols, b->ts);
+    case 5: return gcpb::allow_fused_d<5>(b->bf16, b->cols, b->ts);
+    case 6: return gcpb::allow_fused_d<6>(b->bf16, b->cols, b->ts);
+    case 7: return gcpb::allow_fused_d<7>(b->bf16, b->cols, b->ts);
+    case 8: return gcpb::allow_fused_d<8>(b->bf16, b->cols, b->ts);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_batch_fused(const gcp_batch *b) {
@@ -648,8 +733,10 @@ cudaError_t launch_batch_fused(const gcp_batch *b) {
     switch (b->d) {
 #define GCPB_CASE(D)                                                                                              \
     case D:                                                                                                       \
-        return gcpb::launch_fused_d<D>(b->bf16, b->cols, b->blocks, b->specs, b->tile_start, b->n, b->total_tiles, \
-                                       log2L, b->Rp, b->step, b->tile_loss, b->st);
+        return gcpb::launch_fused_d<D>(b->bf16, b->cols, b->ts, b->blocks, b->specs,                           \
+                                       b->tile_start + gcpb::tile_index(b->ts) * (b->n + 1), b->n,              \
+                                       b->total_tiles[gcpb::tile_index(b->ts)], log2L, b->Rp, b->step,         \
+                                       b->tile_loss, b->st);
         GCPB_CASE(2)
         GCPB_CASE(3)
         GCPB_CASE(4)
@@ -670,7 +757,8 @@ gcp_status enqueue_step(gcp_batch *b) {
     const dim3 gp((unsigned)std::min<int64_t>(64, (b->max_param / 4 + nb - 1) / nb), (unsigned)b->n);
     gcpb::k_batch_zero<<<gp, nb, 0, b->st>>>(b->aux);
     BCUDA(b, launch_batch_fused(b));
-    gcpb::k_batch_post<<<b->nchunks, nb, 0, b->st>>>(b->aux, b->chunks, b->tile_loss, b->client_loss, b->adam);
+    gcpb::k_batch_post<<<b->nchunks, nb, 0, b->st>>>(b->aux, b->chunks, b->tile_loss, b->client_loss, b->adam,
+                                                     gcpb::tile_index(b->ts));
     gcpb::k_batch_advance<<<1, 1, 0, b->st>>>(b->step, b->adam);
     BCUDA(b, cudaGetLastError());
     return GCP_OK;
@@ -700,7 +788,7 @@ gcp_status gcp_batch_create(int32_t nclients, gcp_ctx *const *clients, const int
                          "clients must share order, rank, loss, factor dtype, device and stream");
         if (p[i] < 0 || q[i] < 0 || p[i] + q[i] >= ((int64_t)1 << 31))
             return bfail(nullptr, GCP_ERR_ARG, "per-client sample counts must be >= 0 and sum below 2^31");
-        tiles += (p[i] + q[i] + 31) / 32;
+        tiles += (p[i] + q[i] + 15) / 16;  // the smallest tiles give the most
     }
     if (tiles >= ((int64_t)1 << 31)) return bfail(nullptr, GCP_ERR_ARG, "too many samples in the batch");
     gcp_batch *b = new (std::nothrow) gcp_batch();
@@ -716,18 +804,20 @@ gcp_status gcp_batch_create(int32_t nclients, gcp_ctx *const *clients, const int
     b->clients.assign(clients, clients + nclients);
     b->p.assign(p, p + nclients);
     b->q.assign(q, q + nclients);
-    b->total_tiles = (int)tiles;
     b->cols = c0->cols;
     std::vector<int4> specs((size_t)nclients * gcpb::kSpecWords);
-    std::vector<int> tstart(nclients + 1, 0);
+    std::vector<int> tstart(3 * (nclients + 1), 0);  // per tile size: first tile of each client, then the total
     std::vector<gcpb::ClientAux> aux(nclients);
     for (int i = 0; i < nclients; ++i) {
         gcp_ctx *c = clients[i];
         double w_nz, w_z;
         const gcpk::FusedSpec f = gcpk_make_spec(c, 0, p[i], q[i], true, nullptr, &w_nz, &w_z);
         std::memcpy(&specs[(size_t)i * gcpb::kSpecWords], &f, sizeof(f));
-        const int nt = (int)((p[i] + q[i] + 31) / 32);
-        tstart[i + 1] = tstart[i] + nt;
+        for (int t = 0; t < 3; ++t) {
+            const int ts = gcpb::kTileSizes[t], *row = &tstart[(size_t)t * (nclients + 1)];
+            const int nt = (int)((p[i] + q[i] + ts - 1) / ts);
+            tstart[(size_t)t * (nclients + 1) + i + 1] = row[i] + nt;
+        }
         gcpb::ClientAux &a = aux[i];
         a.A = c->A;
         a.B = c->B;
@@ -743,8 +833,11 @@ gcp_status gcp_batch_create(int32_t nclients, gcp_ctx *const *clients, const int
         a.Rp = c->Rp;
         a.w_nz = w_nz;
         a.w_z = w_z;
-        a.tile0 = tstart[i];
-        a.ntiles = nt;
+        for (int t = 0; t < 3; ++t) {
+            a.tile0[t] = tstart[(size_t)t * (nclients + 1) + i];
+            a.ntiles[t] = tstart[(size_t)t * (nclients + 1) + i + 1] - a.tile0[t];
+            b->total_tiles[t] = tstart[(size_t)t * (nclients + 1) + i + 1];
+        }
         b->max_param = std::max<int64_t>(b->max_param, a.nparam);
         b->max_rep = std::max<int64_t>(b->max_rep, (int64_t)a.Htot * a.Rp);
     }
@@ -768,7 +861,7 @@ gcp_status gcp_batch_create(int32_t nclients, gcp_ctx *const *clients, const int
         (e = cudaMalloc(&b->specs, specs.size() * sizeof(int4))) ||
         (e = cudaMalloc(&b->tile_start, tstart.size() * sizeof(int))) ||
         (e = cudaMalloc(&b->aux, aux.size() * sizeof(gcpb::ClientAux))) ||
-        (e = cudaMalloc(&b->tile_loss, (size_t)std::max(1, b->total_tiles) * sizeof(float2))) ||
+        (e = cudaMalloc(&b->tile_loss, (size_t)std::max(1, b->total_tiles[0]) * sizeof(float2))) ||
         (e = cudaMalloc(&b->client_loss, (size_t)nclients * sizeof(double))) ||
         (e = cudaMalloc(&b->step, 2 * sizeof(uint64_t))) || (e = cudaMalloc(&b->adam, 9 * sizeof(double))) ||
         (e = cudaMallocHost(&b->h_loss, (size_t)nclients * sizeof(double))) ||
@@ -781,7 +874,7 @@ gcp_status gcp_batch_create(int32_t nclients, gcp_ctx *const *clients, const int
         return bfail(nullptr, e == cudaErrorMemoryAllocation ? GCP_ERR_OOM : GCP_ERR_CUDA,
                      std::string("creating the batch: ") + cudaGetErrorString(e));
     }
-    b->blocks = default_blocks(b, b->cols);
+    b->blocks = default_blocks(b, b->cols, b->ts);
     if (prev >= 0) cudaSetDevice(prev);
     *out = b;
     return GCP_OK;
@@ -803,7 +896,17 @@ gcp_status gcp_batch_tune(gcp_batch *b, int32_t lane_cols, int32_t blocks) {
     if (cols != 4 && !(cols == 8 && b->Rp >= 8)) return bfail(b, GCP_ERR_ARG, "lane_cols must be 0, 4 or 8 (8 needs rank > 4)");
     if (blocks < 0) return bfail(b, GCP_ERR_ARG, "blocks must be >= 0");
     b->cols = cols;
-    b->blocks = blocks == 0 ? default_blocks(b, cols) : blocks;
+    b->blocks = blocks == 0 ? default_blocks(b, cols, b->ts) : blocks;
+    return GCP_OK;
+}
+
+gcp_status gcp_batch_tune_tile(gcp_batch *b, int32_t samples_per_warp) {
+    if (!b) return bfail(b, GCP_ERR_ARG, "NULL batch");
+    const int ts = samples_per_warp == 0 ? 32 : samples_per_warp;
+    if (ts != 16 && ts != 32 && ts != 64) return bfail(b, GCP_ERR_ARG, "samples_per_warp must be 0, 16, 32 or 64");
+    const bool auto_blocks = b->blocks == default_blocks(b, b->cols, b->ts);
+    b->ts = ts;
+    if (auto_blocks) b->blocks = default_blocks(b, b->cols, ts);
     return GCP_OK;
 }
 
@@ -816,13 +919,15 @@ gcp_status gcp_batch_local_steps(gcp_batch *b, int32_t tau, const gcp_adam_param
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != b->device) cudaSetDevice(b->device);
-    if (!b->graph || b->graph_tau != tau || b->graph_cols != b->cols || b->graph_blocks != b->blocks) {
+    if (!b->graph || b->graph_tau != tau || b->graph_cols != b->cols || b->graph_blocks != b->blocks ||
+        b->graph_ts != b->ts) {
         if (b->graph) {
             BCUDA(b, cudaStreamSynchronize(b->st));
             cudaGraphExecDestroy(b->graph);
             b->graph = nullptr;
         }
         cudaGraph_t g = nullptr;
+        BCUDA(b, allow_batch_fused(b));  // before the capture: a host call on the kernel
         BCUDA(b, cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
         gcp_status s = GCP_OK;
         for (int k = 0; k < tau && !s; ++k) s = enqueue_step(b);
@@ -838,6 +943,7 @@ gcp_status gcp_batch_local_steps(gcp_batch *b, int32_t tau, const gcp_adam_param
         b->graph_tau = tau;
         b->graph_cols = b->cols;
         b->graph_blocks = b->blocks;
+        b->graph_ts = b->ts;
     }
     BCUDA(b, cudaEventRecord(b->ev_in, b->user_st));  // after the clients' earlier work
     BCUDA(b, cudaStreamWaitEvent(b->st, b->ev_in, 0));

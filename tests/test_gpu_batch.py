@@ -97,12 +97,14 @@ def test_batch_one_step_matches_oracle_client_by_client(env, shards):
 
 
 @pytest.mark.parametrize("dtype", ["fp32", "bf16"])
-def test_batch_folded_gradient_matches_oracle_client_by_client(env, shards, dtype):
+@pytest.mark.parametrize("tile", [16, 32, 64])
+def test_batch_folded_gradient_matches_oracle_client_by_client(env, shards, dtype, tile):
     """The gradient each client's local step folds (multi-client fused pass,
     then k_batch_post's replica fold) and feeds to Adam, read back through a
     readout Adam step (tests/adam_readout.py) and compared element by
-    element with the oracle's sampled gradient, per client and mode.  Every
-    mode of these shards has at most 300 rows, so every row is replicated."""
+    element with the oracle's sampled gradient, per client and mode, with
+    16, 32 and 64 samples per warp tile.  Every mode of these shards has at
+    most 300 rows, so every row is replicated."""
     gcp, torch = env
     bat = make(gcp, shards, dtype)
     ref = []
@@ -112,6 +114,7 @@ def test_batch_folded_gradient_matches_oracle_client_by_client(env, shards, dtyp
         ref.append(oracle.sampled_loss_grad(s["dims"], fac, "poisson", idx, x, w))
     prm = readout_params(gcp, max(np.abs(g).max() for _, Go in ref for g in Go))
     b = gcp.GcpBatch(bat, [s["p"] for s in shards], [s["q"] for s in shards])
+    b.tune(samples_per_warp=tile)
     b.local_steps(1, prm, 13, 0)
     losses = b.losses()
     for c, s, (Lo, Go), L in zip(bat, shards, ref, losses):
@@ -142,8 +145,8 @@ def test_graph_replays_continue_the_step_counters(env, shards):
     b2.close()
 
 
-@pytest.mark.parametrize("cols,blocks", [(8, 0), (4, 3), (8, 1)])
-def test_tuning_knobs_do_not_change_results(env, shards, cols, blocks):
+@pytest.mark.parametrize("cols,blocks,tile", [(8, 0, 32), (4, 3, 32), (8, 1, 64), (4, 0, 16), (8, 5, 16), (4, 0, 64)])
+def test_tuning_knobs_do_not_change_results(env, shards, cols, blocks, tile):
     gcp, torch = env
     adam = gcp.AdamParams(**ADAM)
     base = make(gcp, shards)
@@ -151,7 +154,7 @@ def test_tuning_knobs_do_not_change_results(env, shards, cols, blocks):
     b0.local_steps(2, adam, 3, 0)
     tuned = make(gcp, shards)
     b1 = gcp.GcpBatch(tuned, [s["p"] for s in shards], [s["q"] for s in shards])
-    b1.tune(cols, blocks)
+    b1.tune(cols, blocks, samples_per_warp=tile)
     b1.local_steps(2, adam, 3, 0)
     for c0, c1 in zip(base, tuned):
         a0 = np.concatenate([a.ravel() for a in c0.get_factors()])
@@ -159,6 +162,31 @@ def test_tuning_knobs_do_not_change_results(env, shards, cols, blocks):
         assert rel_err(a1, a0) <= 1e-5
     b0.close()
     b1.close()
+
+
+def test_tile_size_knob_rejects_other_sizes_and_switches_back(env, shards):
+    """gcp_batch_tune_tile takes 16, 32 or 64 (0 = 32); the graph is rebuilt
+    when the size changes, and switching 64 -> 16 -> 32 between calls gives
+    the same models as staying at 32 (up to FP32 summation order)."""
+    gcp, torch = env
+    adam = gcp.AdamParams(**ADAM)
+    a = make(gcp, shards)
+    ba = gcp.GcpBatch(a, [s["p"] for s in shards], [s["q"] for s in shards])
+    for bad in (8, 48, 128, -16):
+        with pytest.raises(gcp.GcpError):
+            ba.tune(samples_per_warp=bad)
+    for k, tile in enumerate((64, 16, 0)):
+        ba.tune(samples_per_warp=tile)
+        ba.local_steps(1, adam, 20 + k, k)
+    r = make(gcp, shards)
+    br = gcp.GcpBatch(r, [s["p"] for s in shards], [s["q"] for s in shards])
+    br.local_steps(3, adam, 20, 0)
+    for c0, c1 in zip(a, r):
+        a0 = np.concatenate([x.ravel() for x in c0.get_factors()])
+        a1 = np.concatenate([x.ravel() for x in c1.get_factors()])
+        assert rel_err(a0, a1) <= 1e-5
+    ba.close()
+    br.close()
 
 
 def test_batch_rejects_mismatched_clients(env, shards):
