@@ -12,9 +12,11 @@
 //   3. a chunked segmented reduction walks the sorted list in chunks of kChunk
 //      (64) positions, one chunk per group of lanes, recomputing the Khatri-Rao row
 //      products.  A run of equal rows that lies inside one chunk is stored to
-//      G directly; a run that crosses a chunk edge leaves a partial vector,
-//      and the partials (again sorted by row) are reduced the same way, level
-//      after level, until one chunk holds them all.
+//      G directly; a run that crosses a chunk edge leaves one partial vector
+//      per chunk it touches (in fixed slots: the right slot of its first
+//      chunk, the left slots of the others);
+//   4. one warp per crossing run, found at the chunk where the run ends,
+//      sums its partials in a fixed order and stores the row.
 // Every step has a fixed shape and order, so the result depends only on the
 // inputs.
 #include <cuda_bf16.h>
@@ -32,7 +34,7 @@ constexpr int kT = 256;            // threads per block
 constexpr int kTile = 4096;        // keys per radix-sort block
 constexpr int kChunk = 64;         // sorted positions per segmented-reduction chunk
 constexpr int kScanBlock = 2048;   // elements per block of the multi-block scan
-constexpr int kAhead = 4;          // carry vectors fetched ahead in the reduction of levels 2+
+constexpr int kAhead = 4;          // partial vectors fetched ahead per lane group in the finishing pass
 
 // --------------------------------------------------------------- radix sort
 // Digits of NB = 256 (8 bits) or 1024 (10 bits) values: keys of up to 10
@@ -53,19 +55,17 @@ __global__ void k_radix_hist(const int32_t *__restrict__ keys, int key_stride, i
 
 // Scan phases: each block of kScanBlock elements scans itself in place and
 // records its total; one block scans the totals (and writes the grand total).
-// in = out scans in place; with `flags`, the input is a carry-key array and
-// each element counts 1 if its key is set (>= 0), else 0.
-// With one block (`total` not NULL), the block also finishes the two-part
-// scan: block_sums[0] = 0 and *total = the grand total.
-__global__ void k_scan_blocks(const int32_t *in, int32_t *out, int64_t n, int32_t *block_sums, bool flags,
-                              int32_t *total) {
+// in = out scans in place.  With one block (`total` not NULL), the block
+// also finishes the two-part scan: block_sums[0] = 0 and *total = the grand
+// total.
+__global__ void k_scan_blocks(const int32_t *in, int32_t *out, int64_t n, int32_t *block_sums, int32_t *total) {
     __shared__ int32_t warp_tot[kT / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * (kScanBlock / kT);
     int32_t v[kScanBlock / kT];
     int32_t sum = 0;
 #pragma unroll
     for (int j = 0; j < kScanBlock / kT; ++j) {
-        v[j] = base + j < n ? (flags ? (in[base + j] >= 0 ? 1 : 0) : in[base + j]) : 0;
+        v[j] = base + j < n ? in[base + j] : 0;
         sum += v[j];
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -124,15 +124,14 @@ __global__ void k_scan_top(int32_t *a, int64_t n, int32_t *total) {
     }
 }
 
-// Exclusive prefix sum of n ints (of `in`, or of the set flags of a carry-key
-// array), left in two parts: a[i] holds the scan
+// Exclusive prefix sum of n ints of `in`, left in two parts: a[i] holds the scan
 // within its block of kScanBlock elements and block_sums[i / kScanBlock]
 // the scan of the block totals, so the full value is their sum (consumers
 // add the two).  *total (if not NULL) receives the grand total.
-void scan_two_part(const int32_t *in, int32_t *a, int64_t n, bool flags, int32_t *total, int32_t *block_sums,
+void scan_two_part(const int32_t *in, int32_t *a, int64_t n, int32_t *total, int32_t *block_sums,
                    cudaStream_t st) {
     const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
-    k_scan_blocks<<<(unsigned)nb, kT, 0, st>>>(in, a, n, block_sums, flags, total);
+    k_scan_blocks<<<(unsigned)nb, kT, 0, st>>>(in, a, n, block_sums, total);
     if (nb > 1) k_scan_top<<<1, kT, 0, st>>>(block_sums, nb, total);
 }
 
@@ -263,31 +262,18 @@ __device__ __forceinline__ void load_cols(const TF *F, int off, const int (&col)
     for (int q = 0; q < NQ; ++q) Quad<TF>::load(F + off + col[q], o + 4 * q);
 }
 
-// Mark a chunk's carry slots that no run used (key -1), so the next level
-// needs no separate clearing pass.  A run touching both edges uses the left
-// slot only.
-__device__ __forceinline__ void clear_unused_slots(int32_t *ckey, int64_t chunk, bool left_used, bool right_used,
-                                                   int glane) {
-    if (glane != 0) return;
-    if (!left_used) ckey[2 * chunk] = -1;
-    if (!right_used) ckey[2 * chunk + 1] = -1;
-}
-
 // Emit one run of equal keys: a run inside the chunk is final (stored to G),
-// a run touching a chunk edge becomes the chunk's left (started earlier) or
-// right (continues later) carry.
+// a run touching a chunk edge leaves the chunk's partial in its left slot
+// (the run started earlier; also when it continues later) or its right slot
+// (the run starts here and continues later).
 template <int NQ>
 __device__ __forceinline__ void emit_run(float *G, int Rp, int row_base, int key, const float (&acc)[4 * NQ],
-                                         const int (&col)[NQ], bool before, bool after, int chunk, int32_t *ckey,
-                                         float *cvec) {
+                                         const int (&col)[NQ], bool before, bool after, int64_t chunk, float *cvec) {
     float *dst;
-    if (!before && !after) {
+    if (!before && !after)
         dst = G + (int64_t)(row_base + key) * Rp;
-    } else {
-        const int slot = 2 * chunk + (before ? 0 : 1);
-        dst = cvec + (int64_t)slot * Rp;
-        if (col[0] == 0) ckey[slot] = key;  // the group's lane 0 records the row
-    }
+    else
+        dst = cvec + (2 * chunk + (before ? 0 : 1)) * Rp;
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
         *reinterpret_cast<float4 *>(dst + col[q]) = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
@@ -302,8 +288,7 @@ __device__ __forceinline__ void emit_run(float *G, int Rp, int row_base, int key
 // them is accumulated.  Products and sums keep the sequential order.
 template <typename TF, int COLS, int D>
 __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32_t *__restrict__ keys,
-                                                    const int32_t *__restrict__ ids, int64_t n, int32_t *ckey,
-                                                    float *cvec) {
+                                                    const int32_t *__restrict__ ids, int64_t n, float *cvec) {
     constexpr int NQ = COLS / 4;
     constexpr int U0 = 32 / ((D - 1) * COLS);
     constexpr int U = U0 < 1 ? 1 : (U0 > 4 ? 4 : U0);  // positions gathered ahead
@@ -333,7 +318,6 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
         for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
         int cur = keys[lo];
         bool before = lo > 0 && keys[lo - 1] == cur;
-        const bool left = before;  // the chunk's left carry slot gets used
         for (int b = 0; b < len; b += L) {
             // this lane's position of the batch: key, y and the D-1 row
             // offsets of the other modes (mode k < n at j = k, k > n at k-1)
@@ -367,7 +351,7 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
                 for (int u = 0; u < U; ++u) {
                     if (t0 + u >= nb) break;
                     if (key[u] != cur) {
-                        emit_run<NQ>(P.G, P.Rp, rown, cur, acc, col, before, false, (int)c, ckey, cvec);
+                        emit_run<NQ>(P.G, P.Rp, rown, cur, acc, col, before, false, c, cvec);
 #pragma unroll
                         for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
                         cur = key[u];
@@ -386,90 +370,79 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
             }
         }
         const bool after = hi < n && keys[hi] == cur;
-        emit_run<NQ>(P.G, P.Rp, rown, cur, acc, col, before, after, (int)c, ckey, cvec);
-        clear_unused_slots(ckey, c, left, after && !before, glane);
+        emit_run<NQ>(P.G, P.Rp, rown, cur, acc, col, before, after, c, cvec);
     }
 }
 
-// Levels 2+: sorted (key, partial vector) list -> G rows and edge carries.
+// Finishing pass: the runs that cross chunk edges.  Warp w looks at chunk
+// c = w: if the chunk's first run began in an earlier chunk and ends in
+// this one, the warp owns that run.  Its first chunk c0 comes from a binary
+// search for the run's first position; its partials are the right slot of
+// c0 and the left slots of c0 + 1 .. c (a chunk the run covers entirely
+// uses its left slot), 1 + c - c0 vectors in all.  The warp's 32 / L lane
+// groups each add every (32 / L)-th of them in order, kAhead at a time; the
+// group sums are then combined by a butterfly over the groups; the order is
+// fixed by (c0, c) alone, so the row is the same from run to run.
 template <int COLS>
-__global__ void __launch_bounds__(kT) k_seg_vectors(const SegSpec P, const int32_t *__restrict__ keys,
-                                                    const float *__restrict__ vecs, const int32_t *__restrict__ dn,
-                                                    int64_t nch_bound, int32_t *ckey, float *cvec) {
+__global__ void __launch_bounds__(kT) k_seg_finish(const SegSpec P, const int32_t *__restrict__ keys, int64_t n,
+                                                   const float *__restrict__ cvec) {
     constexpr int NQ = COLS / 4;
     const int lane = threadIdx.x & 31;
     const int L = 1 << P.log2L;
     const int glane = lane & (L - 1);
-    const int64_t group = ((int64_t)blockIdx.x * kT + threadIdx.x) >> P.log2L;
-    const int64_t ngroups = ((int64_t)gridDim.x * kT) >> P.log2L;
-    const int64_t n = *dn;  // list length, written on the device by the compaction
+    const int grp = lane >> P.log2L, ngrp = 32 >> P.log2L;
     const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    const int64_t c = ((int64_t)blockIdx.x * kT + threadIdx.x) >> 5;  // one warp per chunk
+    if (c >= nchunks) return;
+    const int64_t lo = c * kChunk, hi = lo + kChunk < n ? lo + kChunk : n;
+    const int key = keys[lo];
+    if (lo == 0 || keys[lo - 1] != key) return;          // the chunk's first run starts here
+    if (keys[hi - 1] == key && hi < n && keys[hi] == key) return;  // ... or continues past it
+    int64_t a = 0, b = lo - 1;                           // first position of the run
+    while (a < b) {
+        const int64_t m = (a + b) >> 1;
+        if (keys[m] < key)
+            a = m + 1;
+        else
+            b = m;
+    }
+    const int64_t c0 = a / kChunk;
+    const int64_t np = 1 + c - c0;  // partials: right slot of c0, left slots of c0 + 1 .. c
     int col[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) col[q] = q * (P.Rp >> 1) + 4 * glane;
-    const int rown = P.rown;
-    for (int64_t c = group; c < nchunks; c += ngroups) {
-        const int64_t lo = c * kChunk, hi = lo + kChunk < n ? lo + kChunk : n;
-        float acc[COLS];
+    float acc[COLS];
 #pragma unroll
-        for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
-        int cur = keys[lo];
-        bool before = lo > 0 && keys[lo - 1] == cur;
-        const bool left = before;
-        for (int64_t i0 = lo; i0 < hi; i0 += kAhead) {
-            // fetch kAhead positions' keys and vector slices, then add in order
-            int key[kAhead];
-            float4 t[kAhead][NQ];
+    for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
+    for (int64_t k0 = grp; k0 < np; k0 += (int64_t)kAhead * ngrp) {
+        float4 t[kAhead][NQ];
 #pragma unroll
-            for (int u = 0; u < kAhead; ++u) {
-                const int64_t i = i0 + u < hi ? i0 + u : hi - 1;
-                key[u] = keys[i];
+        for (int u = 0; u < kAhead; ++u) {
+            const int64_t k = k0 + (int64_t)u * ngrp;
+            const int64_t slot = k < np ? (k == 0 ? 2 * c0 + 1 : 2 * (c0 + k)) : 2 * c;
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) t[u][q] = *reinterpret_cast<const float4 *>(vecs + i * P.Rp + col[q]);
-            }
+            for (int q = 0; q < NQ; ++q) t[u][q] = *reinterpret_cast<const float4 *>(cvec + slot * P.Rp + col[q]);
+        }
 #pragma unroll
-            for (int u = 0; u < kAhead; ++u) {
-                if (i0 + u >= hi) break;
-                if (key[u] != cur) {
-                    emit_run<NQ>(P.G, P.Rp, rown, cur, acc, col, before, false, (int)c, ckey, cvec);
+        for (int u = 0; u < kAhead; ++u) {
+            if (k0 + (int64_t)u * ngrp >= np) break;
 #pragma unroll
-                    for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
-                    cur = key[u];
-                    before = false;
-                }
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    acc[4 * q] += t[u][q].x;
-                    acc[4 * q + 1] += t[u][q].y;
-                    acc[4 * q + 2] += t[u][q].z;
-                    acc[4 * q + 3] += t[u][q].w;
-                }
+            for (int q = 0; q < NQ; ++q) {
+                acc[4 * q] += t[u][q].x;
+                acc[4 * q + 1] += t[u][q].y;
+                acc[4 * q + 2] += t[u][q].z;
+                acc[4 * q + 3] += t[u][q].w;
             }
         }
-        const bool after = hi < n && keys[hi] == cur;
-        emit_run<NQ>(P.G, P.Rp, rown, cur, acc, col, before, after, (int)c, ckey, cvec);
-        clear_unused_slots(ckey, c, left, after && !before, glane);
     }
-    // chunks between the list's length and the grid's bound carry nothing
-    for (int64_t c = nchunks + group; c < nch_bound; c += ngroups)
-        clear_unused_slots(ckey, c, false, false, glane);
-}
-
-// Order-preserving compaction of the used carry slots, one 16-byte quad of
-// a vector per thread (Rp = 4 << log2q).
-__global__ void k_carry_compact(const int32_t *ckey, const float *cvec, int64_t n, const int32_t *pos,
-                                const int32_t *pos_blocks, int log2q, int32_t *okey, float *ovec) {
-    const int Rp = 4 << log2q;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (n << log2q);
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e >> log2q;
-        const int c = 4 * (int)(e & ((1 << log2q) - 1));
-        const int32_t key = ckey[i];
-        if (key < 0) continue;
-        const int64_t o = pos[i] + pos_blocks[i / kScanBlock];
-        *reinterpret_cast<float4 *>(ovec + o * Rp + c) = *reinterpret_cast<const float4 *>(cvec + i * Rp + c);
-        if (c == 0) okey[o] = key;
-    }
+    for (int o = L; o < 32; o <<= 1)  // butterfly over the groups, fixed order
+#pragma unroll
+        for (int v = 0; v < COLS; ++v) acc[v] += __shfl_xor_sync(0xFFFFFFFFu, acc[v], o);
+    if (grp != 0) return;
+    float *dst = P.G + (int64_t)(P.rown + key) * P.Rp;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+        *reinterpret_cast<float4 *>(dst + col[q]) = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
 }
 
 int grid_for(int64_t items, int per_block) {
@@ -498,16 +471,8 @@ static gcp_status det_scratch(gcp_ctx *c, int64_t S, size_t *offs) {
     offs[4] = take((size_t)S * 4);                  // keys B
     offs[5] = take((size_t)S * 4);                  // vals B
     offs[6] = take((size_t)1024 * ntiles * 4);      // digit histograms / offsets (up to 1024 digits)
-    offs[7] = take((size_t)2 * nchunk * 4);         // carry keys (level in)
-    offs[8] = take((size_t)2 * nchunk * c->Rp * 4); // carry vectors (level in)
-    offs[9] = take((size_t)2 * nchunk * 4);         // carry keys (level out)
-    offs[10] = take((size_t)2 * nchunk * c->Rp * 4);
-    offs[11] = take((size_t)2 * nchunk * 4);        // compaction positions
-    offs[12] = take((size_t)2 * nchunk * 4);        // compacted keys
-    offs[13] = take((size_t)2 * nchunk * c->Rp * 4);
-    offs[14] = take(16);                            // list length
-    const int64_t scan_n = 1024 * ntiles > 2 * nchunk ? 1024 * ntiles : 2 * nchunk;
-    offs[15] = take((size_t)((scan_n + kScanBlock - 1) / kScanBlock + 1) * 4);  // scan block sums
+    offs[7] = take((size_t)2 * nchunk * c->Rp * 4); // partial vectors: a left and a right slot per chunk
+    offs[8] = take((size_t)((1024 * ntiles + kScanBlock - 1) / kScanBlock + 1) * 4);  // scan block sums
     if (o > c->det_scratch_bytes) {
         cudaFree(c->det_scratch);
         c->det_scratch = nullptr;
@@ -533,24 +498,24 @@ static gcp_status det_scratch(gcp_ctx *c, int64_t S, size_t *offs) {
 
 template <typename TF, int D>
 static void launch_seg_samples_d(const SegSpec &P, int cols, int grid, const int32_t *keys, const int32_t *ids,
-                                 int64_t n, int32_t *ckey, float *cvec, cudaStream_t st) {
+                                 int64_t n, float *cvec, cudaStream_t st) {
     if (cols == 8)
-        k_seg_samples<TF, 8, D><<<grid, kT, 0, st>>>(P, keys, ids, n, ckey, cvec);
+        k_seg_samples<TF, 8, D><<<grid, kT, 0, st>>>(P, keys, ids, n, cvec);
     else
-        k_seg_samples<TF, 4, D><<<grid, kT, 0, st>>>(P, keys, ids, n, ckey, cvec);
+        k_seg_samples<TF, 4, D><<<grid, kT, 0, st>>>(P, keys, ids, n, cvec);
 }
 
 template <typename TF>
 static void launch_seg_samples(const SegSpec &P, int cols, int grid, const int32_t *keys, const int32_t *ids,
-                               int64_t n, int32_t *ckey, float *cvec, cudaStream_t st) {
+                               int64_t n, float *cvec, cudaStream_t st) {
     switch (P.d) {
-        case 2: launch_seg_samples_d<TF, 2>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
-        case 3: launch_seg_samples_d<TF, 3>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
-        case 4: launch_seg_samples_d<TF, 4>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
-        case 5: launch_seg_samples_d<TF, 5>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
-        case 6: launch_seg_samples_d<TF, 6>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
-        case 7: launch_seg_samples_d<TF, 7>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
-        default: launch_seg_samples_d<TF, 8>(P, cols, grid, keys, ids, n, ckey, cvec, st); break;
+        case 2: launch_seg_samples_d<TF, 2>(P, cols, grid, keys, ids, n, cvec, st); break;
+        case 3: launch_seg_samples_d<TF, 3>(P, cols, grid, keys, ids, n, cvec, st); break;
+        case 4: launch_seg_samples_d<TF, 4>(P, cols, grid, keys, ids, n, cvec, st); break;
+        case 5: launch_seg_samples_d<TF, 5>(P, cols, grid, keys, ids, n, cvec, st); break;
+        case 6: launch_seg_samples_d<TF, 6>(P, cols, grid, keys, ids, n, cvec, st); break;
+        case 7: launch_seg_samples_d<TF, 7>(P, cols, grid, keys, ids, n, cvec, st); break;
+        default: launch_seg_samples_d<TF, 8>(P, cols, grid, keys, ids, n, cvec, st); break;
     }
 }
 
@@ -569,7 +534,7 @@ static cudaError_t allow_wide_scatter() {
 
 gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     const int64_t S = f0.s.p + f0.s.q;
-    size_t offs[16];
+    size_t offs[9];
     gcp_status s = det_scratch(c, S > 0 ? S : 1, offs);
     if (s) return s;
     char *base = static_cast<char *>(c->det_scratch);
@@ -578,15 +543,8 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     int32_t *kA = reinterpret_cast<int32_t *>(base + offs[2]), *vA = reinterpret_cast<int32_t *>(base + offs[3]);
     int32_t *kB = reinterpret_cast<int32_t *>(base + offs[4]), *vB = reinterpret_cast<int32_t *>(base + offs[5]);
     int32_t *hist = reinterpret_cast<int32_t *>(base + offs[6]);
-    int32_t *ckey_in = reinterpret_cast<int32_t *>(base + offs[7]);
-    float *cvec_in = reinterpret_cast<float *>(base + offs[8]);
-    int32_t *ckey_out = reinterpret_cast<int32_t *>(base + offs[9]);
-    float *cvec_out = reinterpret_cast<float *>(base + offs[10]);
-    int32_t *cpos = reinterpret_cast<int32_t *>(base + offs[11]);
-    int32_t *lkey = reinterpret_cast<int32_t *>(base + offs[12]);
-    float *lvec = reinterpret_cast<float *>(base + offs[13]);
-    int32_t *dlen = reinterpret_cast<int32_t *>(base + offs[14]);
-    int32_t *bsum = reinterpret_cast<int32_t *>(base + offs[15]);
+    float *cvec = reinterpret_cast<float *>(base + offs[7]);
+    int32_t *bsum = reinterpret_cast<int32_t *>(base + offs[8]);
     cudaStream_t st = c->st;
     DET_CUDA(allow_wide_scatter());
 
@@ -610,8 +568,6 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     P.Yval = Yval;
     P.G = c->G;
     const int lanes = 1 << c->log2L;
-    int log2q = 0;  // Rp = 4 << log2q (Rp is four times a power of two)
-    while ((4 << log2q) < c->Rp) ++log2q;
     for (int n = 0; n < c->d; ++n) {
         P.n_mode = n;
         P.rown = (int)c->rowoff[n];
@@ -626,12 +582,12 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
         for (int shift = 0; shift < bits; shift += wide ? 10 : 8) {
             if (wide) {
                 k_radix_hist<1024><<<(int)ntiles, kT, 0, st>>>(kin, kstride, S, shift, hist, (int)ntiles);
-                scan_two_part(hist, hist, 1024 * ntiles, false, nullptr, bsum, st);
+                scan_two_part(hist, hist, 1024 * ntiles, nullptr, bsum, st);
                 k_radix_scatter<1024><<<(int)ntiles, kT, scatter_smem_bytes<1024>(), st>>>(
                     kin, kstride, vin, S, shift, hist, bsum, (int)ntiles, kout, vout);
             } else {
                 k_radix_hist<256><<<(int)ntiles, kT, 0, st>>>(kin, kstride, S, shift, hist, (int)ntiles);
-                scan_two_part(hist, hist, 256 * ntiles, false, nullptr, bsum, st);
+                scan_two_part(hist, hist, 256 * ntiles, nullptr, bsum, st);
                 k_radix_scatter<256><<<(int)ntiles, kT, scatter_smem_bytes<256>(), st>>>(
                     kin, kstride, vin, S, shift, hist, bsum, (int)ntiles, kout, vout);
             }
@@ -642,34 +598,20 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
             kout = (kout == kA) ? kB : kA;
             vout = (vout == vA) ? vB : vA;
         }
-        // 3. chunked segmented reduction, level 1 over samples
-        int64_t nch = (S + kChunk - 1) / kChunk;
+        // 3. chunked segmented reduction over the sorted samples
+        const int64_t nch = (S + kChunk - 1) / kChunk;
         const int grid = grid_for(nch * lanes, kT);
         if (c->Abf)
-            launch_seg_samples<__nv_bfloat16>(P, c->cols, grid, kin, vin, S, ckey_out, cvec_out, st);
+            launch_seg_samples<__nv_bfloat16>(P, c->cols, grid, kin, vin, S, cvec, st);
         else
-            launch_seg_samples<float>(P, c->cols, grid, kin, vin, S, ckey_out, cvec_out, st);
+            launch_seg_samples<float>(P, c->cols, grid, kin, vin, S, cvec, st);
         DET_CUDA(cudaGetLastError());
-        // levels 2+: compact the carries and reduce them again.  The list
-        // length stays on the device; grids are sized by its upper bound
-        // (two carries per chunk of the previous level), so no host sync.
-        int64_t nslots = 2 * nch;
-        while (nch > 1) {
-            scan_two_part(ckey_out, cpos, nslots, true, dlen, bsum, st);
-            k_carry_compact<<<grid_for(nslots * (c->Rp / 4), kT), kT, 0, st>>>(ckey_out, cvec_out, nslots, cpos,
-                                                                               bsum, log2q, lkey, lvec);
-            nch = (nslots + kChunk - 1) / kChunk;
-            nslots = 2 * nch;
-            std::swap(ckey_in, ckey_out);
-            std::swap(cvec_in, cvec_out);
-            if (c->cols == 8)
-                k_seg_vectors<8><<<grid_for(nch * lanes, kT), kT, 0, st>>>(P, lkey, lvec, dlen, nch, ckey_out,
-                                                                          cvec_out);
-            else
-                k_seg_vectors<4><<<grid_for(nch * lanes, kT), kT, 0, st>>>(P, lkey, lvec, dlen, nch, ckey_out,
-                                                                          cvec_out);
-            DET_CUDA(cudaGetLastError());
-        }
+        // 4. the runs that cross chunk edges: one warp per chunk decides
+        if (c->cols == 8)
+            k_seg_finish<8><<<grid_for(nch * 32, kT), kT, 0, st>>>(P, kin, S, cvec);
+        else
+            k_seg_finish<4><<<grid_for(nch * 32, kT), kT, 0, st>>>(P, kin, S, cvec);
+        DET_CUDA(cudaGetLastError());
     }
     return GCP_OK;
 }
