@@ -340,3 +340,50 @@ def test_batch_padded_rank_empty_client_and_unreplicated_modes(env):
     b.close()
     for c in ref + bat:
         c.close()
+
+
+@pytest.mark.parametrize("ndim,rank,tile", [(2, 8, 64), (5, 12, 16), (5, 12, 64), (4, 32, 64)])
+def test_batch_orders_and_tiles_match_clients_alone(env, ndim, rank, tile):
+    """Order-2, -4 and -5 client shards (the records of order 5 are 64 bytes,
+    the largest staging of a 64-sample tile), padded ranks, 16 and 64
+    samples per warp tile: one local step of the batch equals gcp_grad +
+    gcp_adam_step on every client alone, and the batch's losses equal the
+    oracle's."""
+    gcp, torch = env
+    adam = gcp.AdamParams(**ADAM)
+    cl = synth.client_batch(5, 5100 + ndim, dim_lo=6, dim_hi=40, nnz_lo=200, nnz_hi=3000, ndim=ndim)
+    sh = []
+    for i, (dims, coords, vals) in enumerate(cl):
+        f = synth.factors_uniform(dims, rank, 5200 + i, lo=0.1, hi=1.0)
+        S = max(1, math.ceil(len(vals) / 4))
+        sh.append(dict(dims=dims, coords=coords, vals=vals, factors=f, p=S, q=S + 17 * i, seed=5300 + i))
+
+    def mk():
+        out = []
+        for s in sh:
+            c = gcp.gcp_create(s["dims"], s["coords"], s["vals"], rank, "poisson", seed=s["seed"])
+            c.set_factors(s["factors"])
+            out.append(c)
+        return out
+
+    ref = mk()
+    for c, s in zip(ref, sh):
+        L, _ = c.grad(4, s["p"], s["q"])
+        c.adam_step(adam, 1)
+        s["ref_loss"] = L
+    bat = mk()
+    b = gcp.GcpBatch(bat, [s["p"] for s in sh], [s["q"] for s in sh])
+    b.tune(samples_per_warp=tile)
+    b.local_steps(1, adam, 4, 0)
+    losses = b.losses()
+    for c, r, s, L in zip(bat, ref, sh, losses):
+        A = np.concatenate([a.ravel() for a in c.get_factors()])
+        Ar = np.concatenate([a.ravel() for a in r.get_factors()])
+        assert rel_err(A, Ar) <= 1e-5
+        idx, x, w, _ = oracle.stratified_samples(s["seed"], 4, s["p"], s["q"], s["dims"], s["coords"], s["vals"])
+        Lo, _ = oracle.sampled_loss_grad(s["dims"], s["factors"], "poisson", idx, x, w, grad=False)
+        assert L == pytest.approx(Lo, rel=1e-5)
+        assert L == pytest.approx(s["ref_loss"], rel=1e-6)
+    b.close()
+    for c in ref + bat:
+        c.close()
