@@ -413,15 +413,18 @@ __device__ __forceinline__ void adam_quad(const ClientAux &a, int64_t qi, int co
 //    first lane adds them to the gradient quad and applies Algorithm 1.
 // G itself is cleared at the start of the next step, just before the fused
 // pass, so that its lines are still in L2 when the reductions arrive.
-// Quads per thread of a streaming chunk, all loads issued together: four
-// measured 0.383 ms per local step of the 64-client batch, against 0.414
-// and 0.418 ms with one and two.
-constexpr int kPostUnroll = 4;
+// Quads per thread of a streaming chunk, all loads issued together, with
+// the kernel held to three blocks per SM (78 registers): 0.3725 ms per
+// local step of the 64-client batch, against 0.381 ms with four quads per
+// thread at two blocks per SM, 0.395 ms with two at four blocks and
+// 0.379-0.383 ms with three at two or five and six at two.
+constexpr int kPostUnroll = 3;
+constexpr int kPostMinBlocks = 3;
 constexpr int kPostQuads = kThreads * kPostUnroll;              // quads of a streaming chunk
 constexpr int kHotQuadsPerChunk = kThreads / gcpe::kHotLanes;   // hot quads of a hot chunk
 static_assert(gcpk::kReplicas % gcpe::kHotLanes == 0, "hot-quad replicas split evenly over the folding lanes");
 
-__global__ void __launch_bounds__(kThreads) k_batch_post(const ClientAux *__restrict__ aux,
+__global__ void __launch_bounds__(kThreads, kPostMinBlocks) k_batch_post(const ClientAux *__restrict__ aux,
                                                          const int2 *__restrict__ chunks,
                                                          const float2 *__restrict__ tile_loss, double *client_loss,
                                                          const double *__restrict__ adam, int ti) {
