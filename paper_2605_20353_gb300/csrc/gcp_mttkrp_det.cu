@@ -288,7 +288,8 @@ __device__ __forceinline__ void emit_run(float *G, int Rp, int row_base, int key
 // them is accumulated.  Products and sums keep the sequential order.
 template <typename TF, int COLS, int D>
 __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32_t *__restrict__ keys,
-                                                    const int32_t *__restrict__ ids, int64_t n, float *cvec) {
+                                                    const int32_t *__restrict__ ids, int64_t n, float *cvec,
+                                                    int32_t *rowstart) {
     constexpr int NQ = COLS / 4;
     constexpr int U0 = 32 / ((D - 1) * COLS);
     constexpr int U = U0 < 1 ? 1 : (U0 > 4 ? 4 : U0);  // positions gathered ahead
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
         for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
         int cur = keys[lo];
         bool before = lo > 0 && keys[lo - 1] == cur;
+        if (!before && glane == 0) rowstart[cur] = (int32_t)lo;  // a run starts at the chunk's start
         for (int b = 0; b < len; b += L) {
             // this lane's position of the batch: key, y and the D-1 row
             // offsets of the other modes (mode k < n at j = k, k > n at k-1)
@@ -356,6 +358,7 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
                         for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
                         cur = key[u];
                         before = false;
+                        if (glane == 0) rowstart[cur] = (int32_t)(lo + b + t0 + u);  // a run starts here
                     }
                     float prod[COLS];
 #pragma unroll
@@ -374,85 +377,82 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
     }
 }
 
-// Finishing pass: the runs that cross chunk edges.  Warp w looks at chunk
-// c = w: if the chunk's first run began in an earlier chunk and ends in
-// this one, the warp owns that run.  Its first chunk c0 comes from a binary
-// search for the run's first position; its partials are the right slot of
-// c0 and the left slots of c0 + 1 .. c (a chunk the run covers entirely
-// uses its left slot), 1 + c - c0 vectors in all.  The warp's 32 / L lane
-// groups each add every (32 / L)-th of them in order, kAhead at a time; the
-// group sums are then combined by a butterfly over the groups; the order is
-// fixed by (c0, c) alone, so the row is the same from run to run.
+// Finishing pass: the runs that cross chunk edges.  Lane l of warp w
+// checks chunk c = 32 w + l: it owns a run if the chunk's first run began
+// in an earlier chunk and ends in this one.  The warp then takes its owned
+// chunks one by one.  The run's first chunk c0 comes from the run's start
+// position, which level 1 recorded per row (rowstart); its partials are
+// the right slot of c0 and the left slots of c0 + 1 .. c (a chunk the run
+// covers entirely uses its left slot), 1 + c - c0 vectors in all.  The
+// warp's 32 / L lane groups each add every (32 / L)-th of them in order,
+// kAhead at a time; the group sums are then combined by a butterfly over
+// the groups; the order is fixed by (c0, c) alone, so the row is the same
+// from run to run.
 template <int COLS>
 __global__ void __launch_bounds__(kT) k_seg_finish(const SegSpec P, const int32_t *__restrict__ keys, int64_t n,
-                                                   const float *__restrict__ cvec) {
+                                                   const float *__restrict__ cvec,
+                                                   const int32_t *__restrict__ rowstart) {
     constexpr int NQ = COLS / 4;
     const int lane = threadIdx.x & 31;
     const int L = 1 << P.log2L;
     const int glane = lane & (L - 1);
     const int grp = lane >> P.log2L, ngrp = 32 >> P.log2L;
     const int64_t nchunks = (n + kChunk - 1) / kChunk;
-    const int64_t c = ((int64_t)blockIdx.x * kT + threadIdx.x) >> 5;  // one warp per chunk
-    if (c >= nchunks) return;
-    const int64_t lo = c * kChunk, hi = lo + kChunk < n ? lo + kChunk : n;
-    const int key = keys[lo];
-    if (lo == 0 || keys[lo - 1] != key) return;          // the chunk's first run starts here
-    if (keys[hi - 1] == key && hi < n && keys[hi] == key) return;  // ... or continues past it
-    // First position of the run: a 32-way search over the sorted keys, the
-    // warp's lanes probing 32 evenly spaced positions of [a, b] per round
-    // (about five rounds for 2^22 positions instead of 22 dependent steps).
-    // Invariant: keys[a - 1] < key (or a = 0) and keys[b] == key.
-    int64_t a = 0, b = lo - 1;
-    while (a < b) {
-        const int64_t span = b - a;
-        const int64_t pos = a + (span * (lane + 1)) / 33;  // a <= pos < b
-        const unsigned ge = __ballot_sync(0xFFFFFFFFu, keys[pos] >= key);
-        if (ge == 0) {
-            a = a + (span * 32) / 33 + 1;  // every probe is below the run
-        } else {
-            const int j = __ffs(ge) - 1;   // the first probe inside the run
-            const int64_t hi_pos = a + (span * (j + 1)) / 33;
-            if (j > 0) a = a + (span * j) / 33 + 1;
-            b = hi_pos;
-        }
+    const int64_t warp = ((int64_t)blockIdx.x * kT + threadIdx.x) >> 5;
+    const int64_t cl = warp * 32 + lane;  // the chunk this lane checks
+    bool own = false;
+    int mykey = 0;
+    if (cl < nchunks) {
+        const int64_t lo = cl * kChunk, hi = lo + kChunk < n ? lo + kChunk : n;
+        mykey = keys[lo];
+        own = lo > 0 && keys[lo - 1] == mykey &&            // the first run began earlier
+              !(keys[hi - 1] == mykey && hi < n && keys[hi] == mykey);  // and ends in this chunk
     }
-    const int64_t c0 = a / kChunk;
-    const int64_t np = 1 + c - c0;  // partials: right slot of c0, left slots of c0 + 1 .. c
     int col[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) col[q] = q * (P.Rp >> 1) + 4 * glane;
-    float acc[COLS];
+    for (unsigned owners = __ballot_sync(0xFFFFFFFFu, own); owners; owners &= owners - 1) {
+        const int j = __ffs(owners) - 1;
+        const int64_t c = warp * 32 + j;
+        const int key = __shfl_sync(0xFFFFFFFFu, mykey, j);
+        const int64_t c0 = __ldg(rowstart + key) / kChunk;
+        const int64_t np = 1 + c - c0;  // partials: right slot of c0, left slots of c0 + 1 .. c
+        float acc[COLS];
 #pragma unroll
-    for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
-    for (int64_t k0 = grp; k0 < np; k0 += (int64_t)kAhead * ngrp) {
-        float4 t[kAhead][NQ];
+        for (int v = 0; v < COLS; ++v) acc[v] = 0.0f;
+        for (int64_t k0 = grp; k0 < np; k0 += (int64_t)kAhead * ngrp) {
+            float4 t[kAhead][NQ];
 #pragma unroll
-        for (int u = 0; u < kAhead; ++u) {
-            const int64_t k = k0 + (int64_t)u * ngrp;
-            const int64_t slot = k < np ? (k == 0 ? 2 * c0 + 1 : 2 * (c0 + k)) : 2 * c;
+            for (int u = 0; u < kAhead; ++u) {
+                const int64_t k = k0 + (int64_t)u * ngrp;
+                const int64_t slot = k < np ? (k == 0 ? 2 * c0 + 1 : 2 * (c0 + k)) : 2 * c;
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) t[u][q] = *reinterpret_cast<const float4 *>(cvec + slot * P.Rp + col[q]);
-        }
+                for (int q = 0; q < NQ; ++q)
+                    t[u][q] = *reinterpret_cast<const float4 *>(cvec + slot * P.Rp + col[q]);
+            }
 #pragma unroll
-        for (int u = 0; u < kAhead; ++u) {
-            if (k0 + (int64_t)u * ngrp >= np) break;
+            for (int u = 0; u < kAhead; ++u) {
+                if (k0 + (int64_t)u * ngrp >= np) break;
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                acc[4 * q] += t[u][q].x;
-                acc[4 * q + 1] += t[u][q].y;
-                acc[4 * q + 2] += t[u][q].z;
-                acc[4 * q + 3] += t[u][q].w;
+                for (int q = 0; q < NQ; ++q) {
+                    acc[4 * q] += t[u][q].x;
+                    acc[4 * q + 1] += t[u][q].y;
+                    acc[4 * q + 2] += t[u][q].z;
+                    acc[4 * q + 3] += t[u][q].w;
+                }
             }
         }
+        for (int o = L; o < 32; o <<= 1)  // butterfly over the groups, fixed order
+#pragma unroll
+            for (int v = 0; v < COLS; ++v) acc[v] += __shfl_xor_sync(0xFFFFFFFFu, acc[v], o);
+        if (grp == 0) {
+            float *dst = P.G + (int64_t)(P.rown + key) * P.Rp;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                *reinterpret_cast<float4 *>(dst + col[q]) =
+                    make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
     }
-    for (int o = L; o < 32; o <<= 1)  // butterfly over the groups, fixed order
-#pragma unroll
-        for (int v = 0; v < COLS; ++v) acc[v] += __shfl_xor_sync(0xFFFFFFFFu, acc[v], o);
-    if (grp != 0) return;
-    float *dst = P.G + (int64_t)(P.rown + key) * P.Rp;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q)
-        *reinterpret_cast<float4 *>(dst + col[q]) = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
 }
 
 int grid_for(int64_t items, int per_block) {
@@ -483,6 +483,9 @@ static gcp_status det_scratch(gcp_ctx *c, int64_t S, size_t *offs) {
     offs[6] = take((size_t)1024 * ntiles * 4);      // digit histograms / offsets (up to 1024 digits)
     offs[7] = take((size_t)2 * nchunk * c->Rp * 4); // partial vectors: a left and a right slot per chunk
     offs[8] = take((size_t)((1024 * ntiles + kScanBlock - 1) / kScanBlock + 1) * 4);  // scan block sums
+    int64_t maxdim = 1;
+    for (int k = 0; k < c->d; ++k) maxdim = c->dims[k] > maxdim ? c->dims[k] : maxdim;
+    offs[9] = take((size_t)maxdim * 4);             // start position of each row's run (one mode at a time)
     if (o > c->det_scratch_bytes) {
         cudaFree(c->det_scratch);
         c->det_scratch = nullptr;
@@ -508,24 +511,24 @@ static gcp_status det_scratch(gcp_ctx *c, int64_t S, size_t *offs) {
 
 template <typename TF, int D>
 static void launch_seg_samples_d(const SegSpec &P, int cols, int grid, const int32_t *keys, const int32_t *ids,
-                                 int64_t n, float *cvec, cudaStream_t st) {
+                                 int64_t n, float *cvec, int32_t *rowstart, cudaStream_t st) {
     if (cols == 8)
-        k_seg_samples<TF, 8, D><<<grid, kT, 0, st>>>(P, keys, ids, n, cvec);
+        k_seg_samples<TF, 8, D><<<grid, kT, 0, st>>>(P, keys, ids, n, cvec, rowstart);
     else
-        k_seg_samples<TF, 4, D><<<grid, kT, 0, st>>>(P, keys, ids, n, cvec);
+        k_seg_samples<TF, 4, D><<<grid, kT, 0, st>>>(P, keys, ids, n, cvec, rowstart);
 }
 
 template <typename TF>
 static void launch_seg_samples(const SegSpec &P, int cols, int grid, const int32_t *keys, const int32_t *ids,
-                               int64_t n, float *cvec, cudaStream_t st) {
+                               int64_t n, float *cvec, int32_t *rowstart, cudaStream_t st) {
     switch (P.d) {
-        case 2: launch_seg_samples_d<TF, 2>(P, cols, grid, keys, ids, n, cvec, st); break;
-        case 3: launch_seg_samples_d<TF, 3>(P, cols, grid, keys, ids, n, cvec, st); break;
-        case 4: launch_seg_samples_d<TF, 4>(P, cols, grid, keys, ids, n, cvec, st); break;
-        case 5: launch_seg_samples_d<TF, 5>(P, cols, grid, keys, ids, n, cvec, st); break;
-        case 6: launch_seg_samples_d<TF, 6>(P, cols, grid, keys, ids, n, cvec, st); break;
-        case 7: launch_seg_samples_d<TF, 7>(P, cols, grid, keys, ids, n, cvec, st); break;
-        default: launch_seg_samples_d<TF, 8>(P, cols, grid, keys, ids, n, cvec, st); break;
+        case 2: launch_seg_samples_d<TF, 2>(P, cols, grid, keys, ids, n, cvec, rowstart, st); break;
+        case 3: launch_seg_samples_d<TF, 3>(P, cols, grid, keys, ids, n, cvec, rowstart, st); break;
+        case 4: launch_seg_samples_d<TF, 4>(P, cols, grid, keys, ids, n, cvec, rowstart, st); break;
+        case 5: launch_seg_samples_d<TF, 5>(P, cols, grid, keys, ids, n, cvec, rowstart, st); break;
+        case 6: launch_seg_samples_d<TF, 6>(P, cols, grid, keys, ids, n, cvec, rowstart, st); break;
+        case 7: launch_seg_samples_d<TF, 7>(P, cols, grid, keys, ids, n, cvec, rowstart, st); break;
+        default: launch_seg_samples_d<TF, 8>(P, cols, grid, keys, ids, n, cvec, rowstart, st); break;
     }
 }
 
@@ -544,7 +547,7 @@ static cudaError_t allow_wide_scatter() {
 
 gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     const int64_t S = f0.s.p + f0.s.q;
-    size_t offs[9];
+    size_t offs[10];
     gcp_status s = det_scratch(c, S > 0 ? S : 1, offs);
     if (s) return s;
     char *base = static_cast<char *>(c->det_scratch);
@@ -555,6 +558,7 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     int32_t *hist = reinterpret_cast<int32_t *>(base + offs[6]);
     float *cvec = reinterpret_cast<float *>(base + offs[7]);
     int32_t *bsum = reinterpret_cast<int32_t *>(base + offs[8]);
+    int32_t *rowstart = reinterpret_cast<int32_t *>(base + offs[9]);
     cudaStream_t st = c->st;
     DET_CUDA(allow_wide_scatter());
 
@@ -612,15 +616,16 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
         const int64_t nch = (S + kChunk - 1) / kChunk;
         const int grid = grid_for(nch * lanes, kT);
         if (c->Abf)
-            launch_seg_samples<__nv_bfloat16>(P, c->cols, grid, kin, vin, S, cvec, st);
+            launch_seg_samples<__nv_bfloat16>(P, c->cols, grid, kin, vin, S, cvec, rowstart, st);
         else
-            launch_seg_samples<float>(P, c->cols, grid, kin, vin, S, cvec, st);
+            launch_seg_samples<float>(P, c->cols, grid, kin, vin, S, cvec, rowstart, st);
         DET_CUDA(cudaGetLastError());
-        // 4. the runs that cross chunk edges: one warp per chunk decides
+        // 4. the runs that cross chunk edges: a lane per chunk decides, a warp sums
+        const int fgrid = grid_for(((nch + 31) / 32) * 32, kT);  // a lane per chunk
         if (c->cols == 8)
-            k_seg_finish<8><<<grid_for(nch * 32, kT), kT, 0, st>>>(P, kin, S, cvec);
+            k_seg_finish<8><<<fgrid, kT, 0, st>>>(P, kin, S, cvec, rowstart);
         else
-            k_seg_finish<4><<<grid_for(nch * 32, kT), kT, 0, st>>>(P, kin, S, cvec);
+            k_seg_finish<4><<<fgrid, kT, 0, st>>>(P, kin, S, cvec, rowstart);
         DET_CUDA(cudaGetLastError());
     }
     return GCP_OK;
