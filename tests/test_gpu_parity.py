@@ -484,6 +484,47 @@ def test_deterministic_mttkrp_parity_and_bit_stability(env, dims, R, loss, dtype
     atom.close()
 
 
+def test_deterministic_mttkrp_semi_stratified_scaled_and_missing_samples(env):
+    """The deterministic variant with semi-stratified samples (the
+    f'(x,m) - f'(0,m) correction), a gradient scale from device memory, and
+    a full tensor whose exhausted zero draws are reported and skipped:
+    bit-stable, and equal to the oracle."""
+    gcp, torch = env
+    dims, R = [40, 30, 20], 16
+    coords, vals, factors = problem(dims, 6000, R, "poisson", 771)
+    det = gcp.gcp_create(dims, coords, vals, R, "poisson", seed=23, mttkrp="deterministic", sampling="semi")
+    det.set_factors(factors)
+    scale = torch.tensor([2.5], dtype=torch.float32, device="cuda")
+    G = torch.zeros(det.num_params, dtype=torch.float32, device="cuda")
+    dl = torch.zeros(1, dtype=torch.float64, device="cuda")
+    det.grad_async(3, 2000, 2500, dscale=scale, G_out=G, dloss=dl)
+    det.sync()
+    G2 = torch.zeros_like(G)
+    det.grad_async(3, 2000, 2500, dscale=scale, G_out=G2)
+    det.sync()
+    assert torch.equal(G, G2)
+    idx, x, w, semi = oracle.semi_stratified_samples(23, 3, 2000, 2500, dims, coords, vals)
+    Lo, Go = oracle.sampled_loss_grad(dims, factors, "poisson", idx, x, w, semi=semi)
+    assert abs(dl.item() - Lo) <= TOL_FP32 * abs(Lo)
+    for n, (a, b) in enumerate(zip(split(G.cpu().numpy(), dims, R), Go)):
+        assert rel_err(a, 2.5 * b) <= TOL_FP32, (n, rel_err(a, 2.5 * b))
+    det.close()
+    # every cell a nonzero: each zero draw is exhausted, reported, and adds nothing
+    dims = [3, 2, 2]
+    coords = np.array(list(np.ndindex(*dims)), dtype=np.int32)
+    full = gcp.gcp_create(dims, coords, np.ones(len(coords), np.float32), 2, "poisson", max_attempts=8,
+                          mttkrp="deterministic")
+    full.set_factors(synth.factors_uniform(dims, 2, 772, lo=0.1, hi=1.0))
+    with pytest.raises(gcp.GcpError) as e:
+        full.grad(0, 4, 4)
+    assert e.value.status == "ERR_SAMPLER_EXHAUSTED"
+    L, Gf = gpu_grad(gcp, torch, full, 0, 4, 0)  # still usable
+    idx, x, w, _ = oracle.stratified_samples(0, 0, 4, 0, dims, coords, np.ones(len(coords), np.float32))
+    Lo, Go = oracle.sampled_loss_grad(dims, synth.factors_uniform(dims, 2, 772, lo=0.1, hi=1.0), "poisson", idx, x, w)
+    assert abs(L - Lo) <= TOL_FP32 * abs(Lo)
+    full.close()
+
+
 @pytest.fixture(scope="module")
 def bernoulli_full():
     def make():
