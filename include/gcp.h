@@ -234,8 +234,9 @@ gcp_status gcp_grad_async(gcp_ctx *ctx, uint64_t iter, int64_t p, int64_t q, con
 /* Stage every mode's factor matrix and run the fused pass, in one call (the
  * autograd binding's forward evaluation; the paper has no counterpart).
  * A_modes (host array of ndim pointers) points to the per-mode matrices,
- * I_k x R FP32 row-major, each contiguous, in device or managed memory
- * (GCP_ERR_ARG otherwise); they are copied into the context by one kernel
+ * I_k x R FP32 row-major, each contiguous, in device memory of the
+ * context's device or in managed memory (GCP_ERR_ARG otherwise); they are
+ * copied into the context by one kernel
  * (with the BF16 copy refreshed), asynchronously on the context's stream,
  * so they must stay valid until the stream has consumed them.  Then, as
  * gcp_grad_async with dscale NULL: the sampled loss of iteration `iter` to

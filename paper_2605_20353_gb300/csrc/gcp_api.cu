@@ -805,9 +805,10 @@ gcp_status gcp_grad_factors_async(gcp_ctx *c, const float *const *A_modes, uint6
         if (!A_modes[k]) return fail(c, GCP_ERR_ARG, "NULL factor pointer");
         cudaPointerAttributes at{};
         if (cudaPointerGetAttributes(&at, A_modes[k]) != cudaSuccess ||
-            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) ||
+            (at.type == cudaMemoryTypeDevice && at.device != c->device)) {
             cudaGetLastError();  // a host pointer is an argument error, not a sticky CUDA error
-            return fail(c, GCP_ERR_ARG, "factor matrices must be device or managed memory");
+            return fail(c, GCP_ERR_ARG, "factor matrices must be device or managed memory of the context's device");
         }
         src.A[k] = A_modes[k];
         src.rowoff[k] = c->rowoff[k];
