@@ -1,0 +1,12 @@
+// gcp_batch_fused_t64.cu -- the multi-client fused kernel with 64 samples
+// per warp tile, every order, factor storage and lane-column count.
+#include "gcp_batch_fused.cuh"
+
+namespace gcpb {
+
+template cudaError_t batch_fused_launch<64>(int, bool, int, int, const int4 *, const int *, int, int, int, int,
+                                            const uint64_t *, float2 *, cudaStream_t);
+template cudaError_t batch_fused_allow<64>(int, bool, int);
+template int batch_fused_occupancy<64>(int, bool, int);
+
+}  // namespace gcpb
