@@ -317,6 +317,8 @@ gcp_status run_fused(gcp_ctx *c, uint64_t iter, int64_t p, int64_t q, bool grad,
         m.G = nullptr;
         m.Ycoord = c->nf_coord;
         m.Yval = c->nf_val;
+        m.ystride = c->d;
+        m.vstride = 1;
         GCP_CUDA(c, gcpk::launch_fused(m, c->Abf != nullptr, c->cols, c->max_blocks, c->st, &blocks));
         m.G = c->G;  // pass 2: MTTKRP of the stored gradient tensor
         GCP_CUDA(c, gcpk::launch_mttkrp_nonfused(m, c->hot_slot, c->Abf != nullptr, c->cols, c->max_blocks, c->st));

@@ -47,8 +47,9 @@ struct FusedSpec {
                                     // slots (contiguous), else -1; used for drawn cells
     float *Grep;                    // kReplicas x Htot x Rp replica rows (zero between calls)
     int Htot;                       // replicated rows
-    int32_t *Ycoord;                // materialize mode (G null): per-sample coordinates [S x d]
-    float *Yval;                    //   and gradient-tensor values w f' scale [S] (0 if no sample)
+    int32_t *Ycoord;                // materialize mode (G null): per-sample coordinates
+    float *Yval;                    //   and gradient-tensor values w f' scale (0 if no sample):
+    int ystride, vstride;           //   sample s at Ycoord[s * ystride + k], Yval[s * vstride]
 };
 
 // Rows that many samples hit (Zipf heads, rows of small modes) are

@@ -252,8 +252,8 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
                 const int sm = (tile << 5) + src;
                 if (P.Yval && glane == 0 && sm < S) {  // no sample: a zero entry at a valid cell
 #pragma unroll
-                    for (int k = 0; k < D; ++k) P.Ycoord[(int64_t)sm * D + k] = s_slot[st][warp][src][k];
-                    P.Yval[sm] = 0.0f;
+                    for (int k = 0; k < D; ++k) P.Ycoord[(int64_t)sm * P.ystride + k] = s_slot[st][warp][src][k];
+                    P.Yval[(int64_t)sm * P.vstride] = 0.0f;
                 }
                 continue;
             }
@@ -300,8 +300,8 @@ __global__ void __launch_bounds__(kThreads, (D <= 4 ? (COLS == 4 ? 4 : 3) : 1)) 
                 if (glane == 0) {
                     const int sm = (tile << 5) + src;
 #pragma unroll
-                    for (int k = 0; k < D; ++k) P.Ycoord[(int64_t)sm * D + k] = ii[k];
-                    P.Yval[sm] = ((is_nz || uniform) ? P.w_nz : P.w_z) * df * scale;
+                    for (int k = 0; k < D; ++k) P.Ycoord[(int64_t)sm * P.ystride + k] = ii[k];
+                    P.Yval[(int64_t)sm * P.vstride] = ((is_nz || uniform) ? P.w_nz : P.w_z) * df * scale;
                 }
             } else if (P.G) {
                 const float y = ((is_nz || uniform) ? P.w_nz : P.w_z) * df * scale;
@@ -776,12 +776,12 @@ __global__ void __launch_bounds__(kThreads) k_mttkrp_nonfused(const FusedSpec P,
 #pragma unroll
     for (int q = 0; q < NQ; ++q) col[q] = q * (P.Rp >> 1) + 4 * glane;
     for (int s = group; s < S; s += ngroups) {
-        const float y = __ldg(P.Yval + s);
+        const float y = __ldg(P.Yval + (int64_t)s * P.vstride);
         int ii[D], off[D];
         float a[D][COLS];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            ii[k] = __ldg(P.Ycoord + (int64_t)s * D + k);
+            ii[k] = __ldg(P.Ycoord + (int64_t)s * P.ystride + k);
             off[k] = (P.rowoff[k] + ii[k]) * P.Rp;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) Quad<TF>::load(F + off[k] + col[q], a[k] + 4 * q);

@@ -6,17 +6,20 @@
 // reductions.  This variant fixes the order, so G is bit-identical from run
 // to run, in the spirit of the permutation-based MTTKRP of Sec. 3.1.2:
 //   1. the fused kernel in materialize mode writes every sample's cell and
-//      value y_s = w f'(x_s, m_s) (the non-fused gradient tensor);
-//   2. per mode n, a stable LSD radix sort (8-bit digits) orders the sample
-//      ids by row i_n, ties in sample order;
+//      value y_s = w f'(x_s, m_s) (the non-fused gradient tensor) as one
+//      record of RW words (i_0 .. i_{d-1}, y_s, zeros), so that a later
+//      lookup of a sample reads one 16-byte vector (d <= 3);
+//   2. per mode n, a stable LSD radix sort (8-bit digits, or one 10-bit
+//      pass) orders the sample ids by row i_n, ties in sample order.  The
+//      first pass of every mode is counted and scanned once for all modes;
 //   3. a chunked segmented reduction walks the sorted list in chunks of kChunk
 //      (64) positions, one chunk per group of lanes, recomputing the Khatri-Rao row
 //      products.  A run of equal rows that lies inside one chunk is stored to
 //      G directly; a run that crosses a chunk edge leaves one partial vector
 //      per chunk it touches (in fixed slots: the right slot of its first
 //      chunk, the left slots of the others);
-//   4. one warp per crossing run, found at the chunk where the run ends,
-//      sums its partials in a fixed order and stores the row.
+//   4. a finishing pass sums each crossing run's partials in a fixed order
+//      and stores the row.
 // Every step has a fixed shape and order, so the result depends only on the
 // inputs.
 #include <cuda_bf16.h>
@@ -51,6 +54,57 @@ __global__ void k_radix_hist(const int32_t *__restrict__ keys, int key_stride, i
         atomicAdd(&h[(keys[(first + i) * key_stride] >> shift) & (NB - 1)], 1);
     __syncthreads();
     for (int d = threadIdx.x; d < NB; d += kT) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+// Words of a sample record: d coordinates and y, padded to 4, 8 or 16.
+__host__ __device__ constexpr int rec_words(int d) { return d + 1 <= 4 ? 4 : (d + 1 <= 8 ? 8 : 16); }
+
+// The first pass of every mode (shift 0) counted in one pass over the
+// records: mode k's pass has nb[k] digits and its counts go to
+// hist[base[k] + d * ntiles + t], the modes' count matrices side by side,
+// so that one scan serves them all.  Shared counters of mode k start at
+// soff[k].
+struct FirstPlan {
+    int d, rw;
+    int nb[GCP_MAX_NDIM], soff[GCP_MAX_NDIM];
+    int64_t base[GCP_MAX_NDIM];
+};
+
+__global__ void __launch_bounds__(kT) k_radix_hist_first(const int32_t *__restrict__ recs, int64_t n,
+                                                          const FirstPlan F, int32_t *__restrict__ hist,
+                                                          int ntiles) {
+    __shared__ int h[1024 * GCP_MAX_NDIM];
+    const int d = F.d;
+    const int used = F.soff[d - 1] + F.nb[d - 1];
+    for (int i = threadIdx.x; i < used; i += kT) h[i] = 0;
+    __syncthreads();
+    const int64_t first = (int64_t)blockIdx.x * kTile;
+    const int tile_n = n - first < kTile ? (int)(n - first) : kTile;
+    // kB records per thread at a time, their 16-byte vectors loaded together
+    constexpr int kB = 4;
+    const int4 *__restrict__ r = reinterpret_cast<const int4 *>(recs + first * F.rw);
+    const int nv = F.rw / 4;
+    for (int i0 = threadIdx.x; i0 < tile_n; i0 += kB * kT)
+        for (int v = 0; v < nv && 4 * v < d; ++v) {
+            int4 q[kB];
+#pragma unroll
+            for (int u = 0; u < kB; ++u)
+                q[u] = i0 + u * kT < tile_n ? __ldg(r + (int64_t)(i0 + u * kT) * nv + v) : make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                if (i0 + u * kT >= tile_n) break;
+                const int c[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int k = 4 * v + j;
+                    if (k < d) atomicAdd(&h[F.soff[k] + (c[j] & (F.nb[k] - 1))], 1);
+                }
+            }
+        }
+    __syncthreads();
+    for (int k = 0; k < d; ++k)
+        for (int i = threadIdx.x; i < F.nb[k]; i += kT)
+            hist[F.base[k] + (int64_t)i * ntiles + blockIdx.x] = h[F.soff[k] + i];
 }
 
 // Scan phases: each block of kScanBlock elements scans itself in place and
@@ -119,7 +173,7 @@ __global__ void k_scan_top(int32_t *a, int64_t n, int32_t *total) {
     int64_t run = part[threadIdx.x];
     for (int64_t i = lo; i < hi; ++i) {
         const int32_t v = a[i];
-        a[i] = (int32_t)run;
+        a[i] = static_cast<int32_t>(static_cast<uint32_t>(run));  // modulo 2^32: see k_radix_scatter
         run += v;
     }
 }
@@ -141,6 +195,11 @@ void scan_two_part(const int32_t *in, int32_t *a, int64_t n, int32_t *total, int
 // sorted tile is then written out in order, so consecutive threads store
 // consecutive positions of a digit's run and the global writes are
 // coalesced.  Thread t looks after digits t, t + kT, ... (NB / kT of them).
+// The offset of digit d in this tile is offsets[obase + d * ntiles + tile]
+// plus its block's sum, minus `sub`: the counts of the modes whose count
+// matrices come first in a shared scan (each sums to n).  The sums are
+// taken modulo 2^32, so the difference is exact even where the running
+// total passes 2^31.
 // Shared memory (dynamic): keys and values of the tile, then per digit the
 // next local position, the global shift and one count per warp.
 constexpr int kKeysPerThread = kTile / kT;
@@ -154,7 +213,8 @@ template <int NB>
 __global__ void __launch_bounds__(kT) k_radix_scatter(const int32_t *__restrict__ keys, int key_stride,
                                                       const int32_t *__restrict__ vals, int64_t n, int shift,
                                                       const int32_t *__restrict__ offsets,
-                                                      const int32_t *__restrict__ offset_blocks, int ntiles,
+                                                      const int32_t *__restrict__ offset_blocks, int64_t obase,
+                                                      uint32_t sub, int ntiles,
                                                       int32_t *__restrict__ keys_out, int32_t *__restrict__ vals_out) {
     constexpr int DPT = NB / kT;  // digits per thread
     extern __shared__ __align__(16) int32_t smem[];
@@ -205,8 +265,9 @@ __global__ void __launch_bounds__(kT) k_radix_scatter(const int32_t *__restrict_
 #pragma unroll
     for (int j = 0; j < DPT; ++j) {
         const int d = DPT * threadIdx.x + j;
-        const int64_t oi = (int64_t)d * ntiles + blockIdx.x;
-        gshift[d] = offsets[oi] + offset_blocks[oi / kScanBlock] - start;
+        const int64_t oi = obase + (int64_t)d * ntiles + blockIdx.x;
+        const uint32_t off = (uint32_t)offsets[oi] + (uint32_t)offset_blocks[oi / kScanBlock] - sub;
+        gshift[d] = (int)off - start;
         running[d] = start;
         start += cnt[j];
     }
@@ -251,8 +312,7 @@ struct SegSpec {
     int d, Rp, cols, log2L;
     int rowoff[GCP_MAX_NDIM];
     const void *F;     // factors read by the kernels (FP32 or BF16)
-    const int32_t *Ycoord;
-    const float *Yval;
+    const int32_t *recs;  // sample records: d coordinates, y, padding (rec_words(d) words)
     float *G;
 };
 
@@ -281,9 +341,9 @@ __device__ __forceinline__ void emit_run(float *G, int Rp, int row_base, int key
 
 // Level 1: sorted sample ids of one mode -> G rows and edge carries.
 // The group walks its chunk in batches of L positions.  Each lane first
-// fetches one position's metadata (row key, y_s and the factor-row offsets
-// of the sample's cell), so the dependent id -> sample lookups of a batch
-// overlap; the positions are then taken in order, their metadata broadcast
+// fetches one position's metadata (row key, then the sample's record: y_s
+// and the coordinates that give the factor-row offsets), so the dependent
+// id -> record lookups of a batch overlap; the positions are then taken in order, their metadata broadcast
 // by shuffles and the factor rows of U positions gathered before any of
 // them is accumulated.  Products and sums keep the sequential order.
 template <typename TF, int COLS, int D>
@@ -302,8 +362,8 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
     const int64_t nchunks = (n + kChunk - 1) / kChunk;
     const int nm = P.n_mode;
     const TF *__restrict__ F = static_cast<const TF *>(P.F);
-    const float *__restrict__ Yval = P.Yval;
-    const int32_t *__restrict__ Ycoord = P.Ycoord;
+    constexpr int RW = rec_words(D);
+    const int4 *__restrict__ recs = reinterpret_cast<const int4 *>(P.recs);
     int col[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) col[q] = q * (P.Rp >> 1) + 4 * glane;
@@ -331,10 +391,18 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
             if (pi < hi) {
                 mkey = keys[pi];
                 const int64_t s = ids[pi];
-                my = Yval[s];
+                int w[RW];
 #pragma unroll
-                for (int j = 0; j < D - 1; ++j)
-                    moff[j] = (roff[j] + Ycoord[s * D + (j < nm ? j : j + 1)]) * P.Rp;
+                for (int v = 0; v < RW / 4; ++v) {
+                    const int4 q = __ldg(recs + s * (RW / 4) + v);
+                    w[4 * v] = q.x;
+                    w[4 * v + 1] = q.y;
+                    w[4 * v + 2] = q.z;
+                    w[4 * v + 3] = q.w;
+                }
+                my = __int_as_float(w[D]);
+#pragma unroll
+                for (int j = 0; j < D - 1; ++j) moff[j] = (roff[j] + (j < nm ? w[j] : w[j + 1])) * P.Rp;
             }
             const int nb = len - b < L ? len - b : L;
             for (int t0 = 0; t0 < nb; t0 += U) {
@@ -468,24 +536,26 @@ int grid_for(int64_t items, int per_block) {
 static gcp_status det_scratch(gcp_ctx *c, int64_t S, size_t *offs) {
     const int64_t ntiles = (S + kTile - 1) / kTile;
     const int64_t nchunk = (S + kChunk - 1) / kChunk + 1;
+    const int64_t nfirst = (int64_t)1024 * c->d * ntiles;  // first-pass counts of all modes (at most)
     size_t o = 0;
     auto take = [&](size_t bytes) {
         const size_t at = o;
         o += (bytes + 255) & ~(size_t)255;
         return at;
     };
-    offs[0] = take((size_t)S * c->d * 4);           // Ycoord
-    offs[1] = take((size_t)S * 4);                  // Yval
+    offs[0] = take((size_t)S * rec_words(c->d) * 4);  // sample records
+    offs[1] = take((size_t)256 * ntiles * 4);       // digit counts / offsets of a later pass
     offs[2] = take((size_t)S * 4);                  // keys A
     offs[3] = take((size_t)S * 4);                  // vals A
     offs[4] = take((size_t)S * 4);                  // keys B
     offs[5] = take((size_t)S * 4);                  // vals B
-    offs[6] = take((size_t)1024 * ntiles * 4);      // digit histograms / offsets (up to 1024 digits)
+    offs[6] = take((size_t)nfirst * 4);             // first-pass digit counts / offsets of every mode
     offs[7] = take((size_t)2 * nchunk * c->Rp * 4); // partial vectors: a left and a right slot per chunk
-    offs[8] = take((size_t)((1024 * ntiles + kScanBlock - 1) / kScanBlock + 1) * 4);  // scan block sums
+    offs[8] = take((size_t)((nfirst + kScanBlock - 1) / kScanBlock + 1) * 4);  // their scan block sums
     int64_t maxdim = 1;
     for (int k = 0; k < c->d; ++k) maxdim = c->dims[k] > maxdim ? c->dims[k] : maxdim;
     offs[9] = take((size_t)maxdim * 4);             // start position of each row's run (one mode at a time)
+    offs[10] = take((size_t)((256 * ntiles + kScanBlock - 1) / kScanBlock + 1) * 4);  // later pass block sums
     if (o > c->det_scratch_bytes) {
         cudaFree(c->det_scratch);
         c->det_scratch = nullptr;
@@ -547,30 +617,52 @@ static cudaError_t allow_wide_scatter() {
 
 gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     const int64_t S = f0.s.p + f0.s.q;
-    size_t offs[10];
+    size_t offs[11];
     gcp_status s = det_scratch(c, S > 0 ? S : 1, offs);
     if (s) return s;
     char *base = static_cast<char *>(c->det_scratch);
-    int32_t *Ycoord = reinterpret_cast<int32_t *>(base + offs[0]);
-    float *Yval = reinterpret_cast<float *>(base + offs[1]);
+    const int rw = rec_words(c->d);
+    int32_t *recs = reinterpret_cast<int32_t *>(base + offs[0]);
+    int32_t *histL = reinterpret_cast<int32_t *>(base + offs[1]);
     int32_t *kA = reinterpret_cast<int32_t *>(base + offs[2]), *vA = reinterpret_cast<int32_t *>(base + offs[3]);
     int32_t *kB = reinterpret_cast<int32_t *>(base + offs[4]), *vB = reinterpret_cast<int32_t *>(base + offs[5]);
-    int32_t *hist = reinterpret_cast<int32_t *>(base + offs[6]);
+    int32_t *histF = reinterpret_cast<int32_t *>(base + offs[6]);
     float *cvec = reinterpret_cast<float *>(base + offs[7]);
-    int32_t *bsum = reinterpret_cast<int32_t *>(base + offs[8]);
+    int32_t *bsumF = reinterpret_cast<int32_t *>(base + offs[8]);
     int32_t *rowstart = reinterpret_cast<int32_t *>(base + offs[9]);
+    int32_t *bsumL = reinterpret_cast<int32_t *>(base + offs[10]);
     cudaStream_t st = c->st;
     DET_CUDA(allow_wide_scatter());
 
-    // 1. loss partials and the materialised gradient tensor
+    // 1. loss partials and the materialised gradient tensor, as records
     gcpk::FusedSpec f = f0;
     f.G = nullptr;
-    f.Ycoord = Ycoord;
-    f.Yval = Yval;
+    f.Ycoord = recs;
+    f.Yval = reinterpret_cast<float *>(recs + c->d);
+    f.ystride = rw;
+    f.vstride = rw;
     DET_CUDA(gcpk::launch_fused(f, c->Abf != nullptr, c->cols, c->max_blocks, st, blocks));
     if (S == 0) return GCP_OK;
 
+    // 2a. the first pass of every mode: counted and scanned once
     const int64_t ntiles = (S + kTile - 1) / kTile;
+    int bits[GCP_MAX_NDIM];
+    FirstPlan FP{};
+    FP.d = c->d;
+    FP.rw = rw;
+    int64_t nfirst = 0;
+    for (int k = 0; k < c->d; ++k) {
+        bits[k] = 1;
+        while ((1ll << bits[k]) < c->dims[k]) ++bits[k];
+        FP.nb[k] = bits[k] > 8 && bits[k] <= 10 ? 1024 : 256;  // one 10-bit pass instead of 8 + 2
+        FP.soff[k] = k ? FP.soff[k - 1] + FP.nb[k - 1] : 0;
+        FP.base[k] = nfirst;
+        nfirst += (int64_t)FP.nb[k] * ntiles;
+    }
+    k_radix_hist_first<<<(int)ntiles, kT, 0, st>>>(recs, S, FP, histF, (int)ntiles);
+    scan_two_part(histF, histF, nfirst, nullptr, bsumF, st);
+    DET_CUDA(cudaGetLastError());
+
     SegSpec P{};
     P.d = c->d;
     P.Rp = c->Rp;
@@ -578,33 +670,36 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     P.log2L = c->log2L;
     for (int k = 0; k < c->d; ++k) P.rowoff[k] = (int)c->rowoff[k];
     P.F = f0.F;
-    P.Ycoord = Ycoord;
-    P.Yval = Yval;
+    P.recs = recs;
     P.G = c->G;
     const int lanes = 1 << c->log2L;
     for (int n = 0; n < c->d; ++n) {
         P.n_mode = n;
         P.rown = (int)c->rowoff[n];
-        // 2. stable LSD radix sort of sample ids by row i_n
-        int bits = 1;
-        while ((1ll << bits) < c->dims[n]) ++bits;
-        const int32_t *kin = Ycoord + n;
-        int kstride = c->d;
+        // 2b. stable LSD radix sort of sample ids by row i_n
+        const bool wide = FP.nb[n] == 1024;
+        const int32_t *kin = recs + n;
+        int kstride = rw;
         const int32_t *vin = nullptr;
         int32_t *kout = kA, *vout = vA;
-        const bool wide = bits > 8 && bits <= 10;  // one 10-bit pass instead of 8 + 2
-        for (int shift = 0; shift < bits; shift += wide ? 10 : 8) {
-            if (wide) {
-                k_radix_hist<1024><<<(int)ntiles, kT, 0, st>>>(kin, kstride, S, shift, hist, (int)ntiles);
-                scan_two_part(hist, hist, 1024 * ntiles, nullptr, bsum, st);
-                k_radix_scatter<1024><<<(int)ntiles, kT, scatter_smem_bytes<1024>(), st>>>(
-                    kin, kstride, vin, S, shift, hist, bsum, (int)ntiles, kout, vout);
-            } else {
-                k_radix_hist<256><<<(int)ntiles, kT, 0, st>>>(kin, kstride, S, shift, hist, (int)ntiles);
-                scan_two_part(hist, hist, 256 * ntiles, nullptr, bsum, st);
-                k_radix_scatter<256><<<(int)ntiles, kT, scatter_smem_bytes<256>(), st>>>(
-                    kin, kstride, vin, S, shift, hist, bsum, (int)ntiles, kout, vout);
+        for (int shift = 0; shift < bits[n]; shift += wide ? 10 : 8) {
+            const int32_t *offsets = histF, *blks = bsumF;
+            int64_t obase = FP.base[n];
+            uint32_t sub = (uint32_t)((uint64_t)n * (uint64_t)S);
+            if (shift > 0) {  // a later pass: counted over the previous pass's order
+                k_radix_hist<256><<<(int)ntiles, kT, 0, st>>>(kin, kstride, S, shift, histL, (int)ntiles);
+                scan_two_part(histL, histL, 256 * ntiles, nullptr, bsumL, st);
+                offsets = histL;
+                blks = bsumL;
+                obase = 0;
+                sub = 0;
             }
+            if (wide)
+                k_radix_scatter<1024><<<(int)ntiles, kT, scatter_smem_bytes<1024>(), st>>>(
+                    kin, kstride, vin, S, shift, offsets, blks, obase, sub, (int)ntiles, kout, vout);
+            else
+                k_radix_scatter<256><<<(int)ntiles, kT, scatter_smem_bytes<256>(), st>>>(
+                    kin, kstride, vin, S, shift, offsets, blks, obase, sub, (int)ntiles, kout, vout);
             DET_CUDA(cudaGetLastError());
             kin = kout;
             vin = vout;

@@ -456,6 +456,7 @@ def test_zipf_count_full_size(env, zipf_full, dtype, tol):
     ([60, 50, 40], 64, "bernoulli", "fp32", 3000, 2999),              # 8 columns per lane
     ([23, 17, 11, 7, 5], 16, "gamma", "bf16", 1500, 1001),
     ([5000, 3], 8, "gaussian", "fp32", 1 << 18, 1 << 18),             # rows of ~175k samples: 3 levels
+    ([140000, 6, 5], 8, "gaussian", "fp32", (1 << 17) + 3, (1 << 17) - 1001),  # 18-bit rows: three sort passes
 ])
 def test_deterministic_mttkrp_parity_and_bit_stability(env, dims, R, loss, dtype, p, q):
     gcp, torch = env
