@@ -114,6 +114,106 @@ def peaks():
         return 6800.0, "fallback"
 
 
+class NvmlClocks:
+    """SM clock and clock-event reasons read through NVML (read-only
+    queries, via ctypes) every `period` seconds from a thread while running.
+    The timed loop of the benchmark lasts a few milliseconds, shorter than
+    nvidia-smi's sampling interval; this reader samples inside it.  `ok` is
+    False where NVML or the device cannot be found."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+    NVML_CLOCK_SM = 1
+
+    def __init__(self, device, period=0.0005):
+        self.device = device
+        self.period = period
+        self.ok = False
+        self.samples = []
+        self.max_mhz = None
+
+    def _open(self):
+        import ctypes
+        import threading
+        import torch
+
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            return False
+        self.nv, self.ct = nv, ctypes
+        h = ctypes.c_void_p()
+        uuid = str(torch.cuda.get_device_properties(self.device).uuid)
+        found = False
+        for u in (uuid, "GPU-" + uuid):
+            if nv.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(h)) == 0:
+                found = True
+                break
+        if not found:
+            return False
+        self.h = h
+        mx = ctypes.c_uint()
+        if nv.nvmlDeviceGetMaxClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(mx)) == 0:
+            self.max_mhz = float(mx.value)
+        self.reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.stop = threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        return True
+
+    def _run(self):
+        ct = self.ct
+        clk, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self.stop.is_set():
+            if self.nv.nvmlDeviceGetClockInfo(self.h, self.NVML_CLOCK_SM, ct.byref(clk)) == 0 and \
+                    self.reasons_fn(self.h, ct.byref(rs)) == 0:
+                self.samples.append((float(clk.value), int(rs.value)))
+            time.sleep(self.period)
+
+    def __enter__(self):
+        try:
+            self.ok = self._open()
+        except (OSError, AttributeError, RuntimeError):
+            self.ok = False
+        if self.ok:
+            self.thread.start()
+            t0 = time.perf_counter()
+            while not self.samples and time.perf_counter() - t0 < 1.0:  # running before the loop starts
+                time.sleep(self.period)
+        return self
+
+    def __exit__(self, *a):
+        if self.ok:
+            self.stop.set()
+            self.thread.join(timeout=2)
+            self.nv.nvmlShutdown()
+
+    def summary(self):
+        sm = [c for c, _ in self.samples]
+        reasons = sorted({n for _, r in self.samples for bit, n in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": self.max_mhz if self.max_mhz else (max(sm) if sm else None),
+                "reasons": reasons, "samples": len(sm), "source": "nvml, every 0.5 ms"}
+
+
+class ClockRecord:
+    """Clocks during a timed region: NVML when it can be read, else
+    nvidia-smi every 20 ms."""
+
+    def __init__(self, device):
+        self.device = device
+
+    def __enter__(self):
+        self.src = NvmlClocks(self.device).__enter__()
+        if not self.src.ok:
+            self.src = ClockSampler(self.device).__enter__()
+        return self
+
+    def __exit__(self, *a):
+        self.src.__exit__(*a)
+
+    def summary(self):
+        return self.src.summary()
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples every 20 ms while running."""
 
@@ -161,7 +261,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, every 20 ms"}
 
 
 def cpu_oracle_rate(w, skeys, n_samples, seed=3002, t=5):
@@ -845,7 +945,7 @@ def run_ours(args):
         ctx.close()
         return
     ctx = make("fp32")
-    with ClockSampler(local) as clk:
+    with ClockRecord(local) as clk:
         ms, kernel_ms, launches = timed_loop(ctx, args.steps, args.warmup, profile=True)
     clocks = clk.summary()
     value, slowest_s = combine_ranks(ms / 1e3, S * args.steps, world, dist, device="cuda")

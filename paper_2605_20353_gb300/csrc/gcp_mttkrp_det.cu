@@ -40,20 +40,73 @@ constexpr int kScanBlock = 2048;   // elements per block of the multi-block scan
 constexpr int kAhead = 4;          // partial vectors fetched ahead per lane group in the finishing pass
 
 // --------------------------------------------------------------- radix sort
+// One sort pass can sort several modes side by side (so that its blocks
+// fill the GPU's waves): segment q sorts one mode's keys (kin, kstride words
+// apart) with their values (vin, or the sample ids when null) into kout /
+// vout.  Its digit counts start at obase in the count matrix, and `sub` is
+// taken off its scanned offsets (k_radix_scatter).  Blocks [q * per, (q +
+// 1) * per) of a launch work on segment q.
+struct SortSeg {
+    const int32_t *kin, *vin;
+    int32_t *kout, *vout;
+    int64_t obase;
+    uint32_t sub;
+    int kstride;
+};
+struct SortSegs {
+    int nseg;
+    SortSeg s[GCP_MAX_NDIM];
+};
+
+// Segment q, read with constant indices only: a runtime index into a kernel
+// parameter array would copy the whole array to local memory per thread.
+__device__ __forceinline__ SortSeg pick_seg(const SortSegs &S, int q) {
+    SortSeg r = S.s[0];
+#pragma unroll
+    for (int i = 1; i < GCP_MAX_NDIM; ++i)
+        if (q == i) r = S.s[i];
+    return r;
+}
+
 // Digits of NB = 256 (8 bits) or 1024 (10 bits) values: keys of up to 10
-// bits sort in one pass, longer ones in 8-bit passes.  hist[d * ntiles + t]
-// counts digit d in tile t.
+// bits sort in one pass, longer ones in 8-bit passes.  Segment q's count of
+// digit d in tile t goes to hist[obase_q + d * ntiles + t].  A block counts
+// kHistTiles consecutive tiles, so that it writes kHistTiles consecutive
+// counts of each digit together.
+constexpr int kHistTiles = 4;
+
 template <int NB>
-__global__ void k_radix_hist(const int32_t *__restrict__ keys, int key_stride, int64_t n, int shift,
-                             int32_t *__restrict__ hist, int ntiles) {
-    __shared__ int h[NB];
-    for (int d = threadIdx.x; d < NB; d += kT) h[d] = 0;
+__global__ void k_radix_hist(const SortSegs SG, int64_t n, int shift, int32_t *__restrict__ hist, int ntiles) {
+    __shared__ int h[kHistTiles][NB];
+    for (int i = threadIdx.x; i < kHistTiles * NB; i += kT) (&h[0][0])[i] = 0;
     __syncthreads();
-    const int64_t first = (int64_t)blockIdx.x * kTile;
-    for (int i = threadIdx.x; i < kTile && first + i < n; i += kT)
-        atomicAdd(&h[(keys[(first + i) * key_stride] >> shift) & (NB - 1)], 1);
+    const int per = (ntiles + kHistTiles - 1) / kHistTiles;
+    const SortSeg sg = pick_seg(SG, blockIdx.x / per);
+    const int32_t *__restrict__ keys = sg.kin;
+    const int key_stride = sg.kstride;
+    const int t0 = (blockIdx.x % per) * kHistTiles;
+    const int64_t first = (int64_t)t0 * kTile;
+    constexpr int kB = 4;  // keys per tile loaded together, for every tile of the block
+    for (int i0 = threadIdx.x; i0 < kTile; i0 += kB * kT) {
+        int k[kHistTiles][kB];
+#pragma unroll
+        for (int g = 0; g < kHistTiles; ++g)
+#pragma unroll
+            for (int u = 0; u < kB; ++u) {
+                const int64_t i = first + (int64_t)g * kTile + i0 + u * kT;
+                k[g][u] = i < n ? keys[i * key_stride] : -1;
+            }
+#pragma unroll
+        for (int g = 0; g < kHistTiles; ++g)
+#pragma unroll
+            for (int u = 0; u < kB; ++u)
+                if (k[g][u] >= 0) atomicAdd(&h[g][(k[g][u] >> shift) & (NB - 1)], 1);
+    }
     __syncthreads();
-    for (int d = threadIdx.x; d < NB; d += kT) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
+    for (int i = threadIdx.x; i < kHistTiles * NB; i += kT) {
+        const int d = i / kHistTiles, g = i % kHistTiles;
+        if (t0 + g < ntiles) hist[sg.obase + (int64_t)d * ntiles + t0 + g] = h[g][d];
+    }
 }
 
 // Words of a sample record: d coordinates and y, padded to 4, 8 or 16.
@@ -72,48 +125,58 @@ struct FirstPlan {
 
 __global__ void __launch_bounds__(kT) k_radix_hist_first(const int32_t *__restrict__ recs, int64_t n,
                                                           const FirstPlan F, int32_t *__restrict__ hist,
-                                                          int ntiles) {
-    __shared__ int h[1024 * GCP_MAX_NDIM];
+                                                          int ntiles, int G) {
+    extern __shared__ int h[];  // [G][used]
     const int d = F.d;
     const int used = F.soff[d - 1] + F.nb[d - 1];
-    for (int i = threadIdx.x; i < used; i += kT) h[i] = 0;
+    for (int i = threadIdx.x; i < G * used; i += kT) h[i] = 0;
     __syncthreads();
-    const int64_t first = (int64_t)blockIdx.x * kTile;
-    const int tile_n = n - first < kTile ? (int)(n - first) : kTile;
+    const int t0 = blockIdx.x * G;
     // kB records per thread at a time, their 16-byte vectors loaded together
     constexpr int kB = 4;
-    const int4 *__restrict__ r = reinterpret_cast<const int4 *>(recs + first * F.rw);
     const int nv = F.rw / 4;
-    for (int i0 = threadIdx.x; i0 < tile_n; i0 += kB * kT)
-        for (int v = 0; v < nv && 4 * v < d; ++v) {
-            int4 q[kB];
+    for (int g = 0; g < G; ++g) {
+        const int64_t first = (int64_t)(t0 + g) * kTile;
+        const int tile_n = first >= n ? 0 : (n - first < kTile ? (int)(n - first) : kTile);
+        const int4 *__restrict__ r = reinterpret_cast<const int4 *>(recs + first * F.rw);
+        int *hg = h + g * used;
+        for (int i0 = threadIdx.x; i0 < tile_n; i0 += kB * kT)
+            for (int v = 0; v < nv && 4 * v < d; ++v) {
+                int4 q[kB];
 #pragma unroll
-            for (int u = 0; u < kB; ++u)
-                q[u] = i0 + u * kT < tile_n ? __ldg(r + (int64_t)(i0 + u * kT) * nv + v) : make_int4(0, 0, 0, 0);
+                for (int u = 0; u < kB; ++u)
+                    q[u] = i0 + u * kT < tile_n ? __ldg(r + (int64_t)(i0 + u * kT) * nv + v) : make_int4(0, 0, 0, 0);
 #pragma unroll
-            for (int u = 0; u < kB; ++u) {
-                if (i0 + u * kT >= tile_n) break;
-                const int c[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+                for (int u = 0; u < kB; ++u) {
+                    if (i0 + u * kT >= tile_n) break;
+                    const int c[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int k = 4 * v + j;
-                    if (k < d) atomicAdd(&h[F.soff[k] + (c[j] & (F.nb[k] - 1))], 1);
+                    for (int j = 0; j < 4; ++j) {
+                        const int k = 4 * v + j;
+                        if (k < d) atomicAdd(&hg[F.soff[k] + (c[j] & (F.nb[k] - 1))], 1);
+                    }
                 }
             }
-        }
+    }
     __syncthreads();
+    // G consecutive counts of a digit are written together
     for (int k = 0; k < d; ++k)
-        for (int i = threadIdx.x; i < F.nb[k]; i += kT)
-            hist[F.base[k] + (int64_t)i * ntiles + blockIdx.x] = h[F.soff[k] + i];
+        for (int i = threadIdx.x; i < F.nb[k] * G; i += kT) {
+            const int dg = i / G, g = i % G;
+            if (t0 + g < ntiles) hist[F.base[k] + (int64_t)dg * ntiles + t0 + g] = h[g * used + F.soff[k] + dg];
+        }
 }
 
-// Scan phases: each block of kScanBlock elements scans itself in place and
-// records its total; one block scans the totals (and writes the grand total).
-// in = out scans in place.  With one block (`total` not NULL), the block
-// also finishes the two-part scan: block_sums[0] = 0 and *total = the grand
-// total.
-__global__ void k_scan_blocks(const int32_t *in, int32_t *out, int64_t n, int32_t *block_sums, int32_t *total) {
+// Exclusive prefix sum of n ints of `in` (in = out scans in place), left in
+// two parts: out[i] holds the scan within its block of kScanBlock elements
+// and block_sums[i / kScanBlock] the scan of the block totals, so the full
+// value is their sum (consumers add the two).  Each block scans its
+// elements and records its total; the last block to finish (a ticket on
+// `done`, which it clears again for the next scan) then scans the totals.
+// Sums are taken modulo 2^32 (see k_radix_scatter).
+__global__ void k_scan_blocks(const int32_t *in, int32_t *out, int64_t n, int32_t *block_sums, unsigned *done) {
     __shared__ int32_t warp_tot[kT / 32];
+    __shared__ bool last;
     const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * (kScanBlock / kT);
     int32_t v[kScanBlock / kT];
     int32_t sum = 0;
@@ -143,50 +206,43 @@ __global__ void k_scan_blocks(const int32_t *in, int32_t *out, int64_t n, int32_
         run += v[j];
     }
     if (threadIdx.x == 0) {
-        if (gridDim.x == 1) {
-            block_sums[0] = 0;
-            if (total) *total = block_total;
-        } else {
-            block_sums[blockIdx.x] = block_total;
-        }
+        block_sums[blockIdx.x] = block_total;
+        __threadfence();  // the total is visible before the ticket is taken
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+        if (last) __threadfence();  // and the other blocks' totals are seen after it
     }
-}
-
-__global__ void k_scan_top(int32_t *a, int64_t n, int32_t *total) {
+    __syncthreads();
+    if (!last) return;
+    // the last block: exclusive scan of the gridDim.x totals, in place
     __shared__ int64_t part[kT];
-    const int64_t per = (n + kT - 1) / kT;
-    const int64_t lo = (int64_t)threadIdx.x * per, hi = lo + per < n ? lo + per : n;
+    const int64_t nb = gridDim.x;
+    const int64_t per = (nb + kT - 1) / kT;
+    const int64_t lo = (int64_t)threadIdx.x * per, hi = lo + per < nb ? lo + per : nb;
     int64_t s = 0;
-    for (int64_t i = lo; i < hi; ++i) s += a[i];
+    for (int64_t i = lo; i < hi; ++i) s += __ldcg(block_sums + i);
     part[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int64_t run = 0;
+        int64_t r = 0;
         for (int t = 0; t < kT; ++t) {
-            const int64_t v = part[t];
-            part[t] = run;
-            run += v;
+            const int64_t x = part[t];
+            part[t] = r;
+            r += x;
         }
-        if (total) *total = (int32_t)run;
+        *done = 0u;
     }
     __syncthreads();
-    int64_t run = part[threadIdx.x];
+    int64_t r = part[threadIdx.x];
     for (int64_t i = lo; i < hi; ++i) {
-        const int32_t v = a[i];
-        a[i] = static_cast<int32_t>(static_cast<uint32_t>(run));  // modulo 2^32: see k_radix_scatter
-        run += v;
+        const int32_t x = __ldcg(block_sums + i);
+        block_sums[i] = static_cast<int32_t>(static_cast<uint32_t>(r));
+        r += x;
     }
 }
 
-// Exclusive prefix sum of n ints of `in`, left in two parts: a[i] holds the scan
-// within its block of kScanBlock elements and block_sums[i / kScanBlock]
-// the scan of the block totals, so the full value is their sum (consumers
-// add the two).  *total (if not NULL) receives the grand total.
-void scan_two_part(const int32_t *in, int32_t *a, int64_t n, int32_t *total, int32_t *block_sums,
-                   cudaStream_t st) {
+void scan_two_part(const int32_t *in, int32_t *a, int64_t n, int32_t *block_sums, unsigned *done, cudaStream_t st) {
     const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
-    k_scan_blocks<<<(unsigned)nb, kT, 0, st>>>(in, a, n, block_sums, total);
-    if (nb > 1) k_scan_top<<<1, kT, 0, st>>>(block_sums, nb, total);
+    k_scan_blocks<<<(unsigned)nb, kT, 0, st>>>(in, a, n, block_sums, done);
 }
 
 // Stable scatter of one digit pass (NB digit values).  The tile's keys are
@@ -195,9 +251,10 @@ void scan_two_part(const int32_t *in, int32_t *a, int64_t n, int32_t *total, int
 // sorted tile is then written out in order, so consecutive threads store
 // consecutive positions of a digit's run and the global writes are
 // coalesced.  Thread t looks after digits t, t + kT, ... (NB / kT of them).
-// The offset of digit d in this tile is offsets[obase + d * ntiles + tile]
-// plus its block's sum, minus `sub`: the counts of the modes whose count
-// matrices come first in a shared scan (each sums to n).  The sums are
+// Block b sorts tile b % ntiles of segment b / ntiles.  The offset of digit
+// d in this tile is offsets[obase + d * ntiles + tile] plus its block's
+// sum, minus `sub`: the counts of the segments (modes) whose count matrices
+// come first in a shared scan (each sums to n).  The sums are
 // taken modulo 2^32, so the difference is exact even where the running
 // total passes 2^31.
 // Shared memory (dynamic): keys and values of the tile, then per digit the
@@ -210,12 +267,16 @@ constexpr size_t scatter_smem_bytes() {
 }
 
 template <int NB>
-__global__ void __launch_bounds__(kT) k_radix_scatter(const int32_t *__restrict__ keys, int key_stride,
-                                                      const int32_t *__restrict__ vals, int64_t n, int shift,
+__global__ void __launch_bounds__(kT, NB == 256 ? 5 : 3) k_radix_scatter(const SortSegs SG, int64_t n, int shift,
                                                       const int32_t *__restrict__ offsets,
-                                                      const int32_t *__restrict__ offset_blocks, int64_t obase,
-                                                      uint32_t sub, int ntiles,
-                                                      int32_t *__restrict__ keys_out, int32_t *__restrict__ vals_out) {
+                                                      const int32_t *__restrict__ offset_blocks, int ntiles) {
+    const SortSeg sg = pick_seg(SG, blockIdx.x / ntiles);
+    const int tile = blockIdx.x % ntiles;
+    const int32_t *__restrict__ keys = sg.kin;
+    const int32_t *__restrict__ vals = sg.vin;
+    int32_t *__restrict__ keys_out = sg.kout;
+    int32_t *__restrict__ vals_out = sg.vout;
+    const int key_stride = sg.kstride;
     constexpr int DPT = NB / kT;  // digits per thread
     extern __shared__ __align__(16) int32_t smem[];
     int32_t *s_key = smem, *s_val = smem + kTile;
@@ -224,7 +285,7 @@ __global__ void __launch_bounds__(kT) k_radix_scatter(const int32_t *__restrict_
     int *wcount = gshift + NB;                // [kT / 32][NB]
     int *wsum = wcount + (kT / 32) * NB;      // [kT / 32]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t first = (int64_t)blockIdx.x * kTile;
+    const int64_t first = (int64_t)tile * kTile;
     const int tile_n = n - first < kTile ? (int)(n - first) : kTile;
     int32_t key[kKeysPerThread], val[kKeysPerThread];
     for (int d = threadIdx.x; d < NB; d += kT) {
@@ -265,8 +326,8 @@ __global__ void __launch_bounds__(kT) k_radix_scatter(const int32_t *__restrict_
 #pragma unroll
     for (int j = 0; j < DPT; ++j) {
         const int d = DPT * threadIdx.x + j;
-        const int64_t oi = obase + (int64_t)d * ntiles + blockIdx.x;
-        const uint32_t off = (uint32_t)offsets[oi] + (uint32_t)offset_blocks[oi / kScanBlock] - sub;
+        const int64_t oi = sg.obase + (int64_t)d * ntiles + tile;
+        const uint32_t off = (uint32_t)offsets[oi] + (uint32_t)offset_blocks[oi / kScanBlock] - sg.sub;
         gshift[d] = (int)off - start;
         running[d] = start;
         start += cnt[j];
@@ -347,7 +408,7 @@ __device__ __forceinline__ void emit_run(float *G, int Rp, int row_base, int key
 // by shuffles and the factor rows of U positions gathered before any of
 // them is accumulated.  Products and sums keep the sequential order.
 template <typename TF, int COLS, int D>
-__global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32_t *__restrict__ keys,
+__global__ void __launch_bounds__(kT, COLS == 8 && D >= 5 ? 2 : 3) k_seg_samples(const SegSpec P, const int32_t *__restrict__ keys,
                                                     const int32_t *__restrict__ ids, int64_t n, float *cvec,
                                                     int32_t *rowstart) {
     constexpr int NQ = COLS / 4;
@@ -380,29 +441,41 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
         int cur = keys[lo];
         bool before = lo > 0 && keys[lo - 1] == cur;
         if (!before && glane == 0) rowstart[cur] = (int32_t)lo;  // a run starts at the chunk's start
+        // the first batch's metadata: key and id, then the record
+        int nkey = 0;
+        int64_t nid = 0;
+        int4 nrec[RW / 4];
+        if (lo + glane < hi) {
+            nkey = keys[lo + glane];
+            nid = ids[lo + glane];
+        }
+#pragma unroll
+        for (int v = 0; v < RW / 4; ++v)
+            nrec[v] = lo + glane < hi ? __ldg(recs + nid * (RW / 4) + v) : make_int4(0, 0, 0, 0);
         for (int b = 0; b < len; b += L) {
-            // this lane's position of the batch: key, y and the D-1 row
-            // offsets of the other modes (mode k < n at j = k, k > n at k-1)
-            const int64_t pi = lo + b + glane;
-            int mkey = 0, moff[D - 1];
-            float my = 0.0f;
+            // this lane's position of the batch (its metadata was fetched
+            // during the previous batch): key, y and the D-1 row offsets of
+            // the other modes (mode k < n at j = k, k > n at k-1)
+            const int mkey = nkey;
+            int w[RW];
 #pragma unroll
-            for (int j = 0; j < D - 1; ++j) moff[j] = 0;
-            if (pi < hi) {
-                mkey = keys[pi];
-                const int64_t s = ids[pi];
-                int w[RW];
+            for (int v = 0; v < RW / 4; ++v) {
+                w[4 * v] = nrec[v].x;
+                w[4 * v + 1] = nrec[v].y;
+                w[4 * v + 2] = nrec[v].z;
+                w[4 * v + 3] = nrec[v].w;
+            }
+            const float my = __int_as_float(w[D]);
+            int moff[D - 1];
 #pragma unroll
-                for (int v = 0; v < RW / 4; ++v) {
-                    const int4 q = __ldg(recs + s * (RW / 4) + v);
-                    w[4 * v] = q.x;
-                    w[4 * v + 1] = q.y;
-                    w[4 * v + 2] = q.z;
-                    w[4 * v + 3] = q.w;
-                }
-                my = __int_as_float(w[D]);
-#pragma unroll
-                for (int j = 0; j < D - 1; ++j) moff[j] = (roff[j] + (j < nm ? w[j] : w[j + 1])) * P.Rp;
+            for (int j = 0; j < D - 1; ++j) moff[j] = (roff[j] + (j < nm ? w[j] : w[j + 1])) * P.Rp;
+            // the next batch's key and id now; its record once the first
+            // rows of this batch are on their way
+            const int64_t pn = lo + b + L + glane;
+            const bool has_next = pn < hi;
+            if (has_next) {
+                nkey = keys[pn];
+                nid = ids[pn];
             }
             const int nb = len - b < L ? len - b : L;
             for (int t0 = 0; t0 < nb; t0 += U) {
@@ -417,6 +490,10 @@ __global__ void __launch_bounds__(kT) k_seg_samples(const SegSpec P, const int32
                     for (int j = 0; j < D - 1; ++j)
                         load_cols<TF, NQ>(F, __shfl_sync(gmask, moff[j], t, L), col, a[u][j]);
                 }
+                if (t0 == 0)
+#pragma unroll
+                    for (int v = 0; v < RW / 4; ++v)
+                        nrec[v] = has_next ? __ldg(recs + nid * (RW / 4) + v) : make_int4(0, 0, 0, 0);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (t0 + u >= nb) break;
@@ -532,30 +609,39 @@ int grid_for(int64_t items, int per_block) {
 
 }  // namespace
 
-// Scratch for the deterministic variant, grown on demand.
+// Modes sorted side by side: as many as fit sort buffers of 1 GiB (each
+// mode needs two key/id pairs of S ints), at least one.
+static int det_group(const gcp_ctx *c, int64_t S) {
+    const int64_t per_mode = 16 * (S > 0 ? S : 1);
+    const int64_t g = ((int64_t)1 << 30) / per_mode;
+    return (int)(g < 1 ? 1 : (g > c->d ? c->d : g));
+}
+
+// Scratch for the deterministic variant, grown on demand.  The scans'
+// ticket comes first, so that it keeps its place (and its zero) whatever
+// the sample count.
 static gcp_status det_scratch(gcp_ctx *c, int64_t S, size_t *offs) {
     const int64_t ntiles = (S + kTile - 1) / kTile;
     const int64_t nchunk = (S + kChunk - 1) / kChunk + 1;
     const int64_t nfirst = (int64_t)1024 * c->d * ntiles;  // first-pass counts of all modes (at most)
+    const int g = det_group(c, S);
     size_t o = 0;
     auto take = [&](size_t bytes) {
         const size_t at = o;
         o += (bytes + 255) & ~(size_t)255;
         return at;
     };
-    offs[0] = take((size_t)S * rec_words(c->d) * 4);  // sample records
-    offs[1] = take((size_t)256 * ntiles * 4);       // digit counts / offsets of a later pass
-    offs[2] = take((size_t)S * 4);                  // keys A
-    offs[3] = take((size_t)S * 4);                  // vals A
-    offs[4] = take((size_t)S * 4);                  // keys B
-    offs[5] = take((size_t)S * 4);                  // vals B
-    offs[6] = take((size_t)nfirst * 4);             // first-pass digit counts / offsets of every mode
+    offs[0] = take(4);                              // the scans' finishing ticket (zero between scans)
+    offs[1] = take((size_t)S * rec_words(c->d) * 4);  // sample records
+    offs[2] = take((size_t)g * 4 * S * 4);          // per mode of a group: keys and ids, two of each
+    offs[3] = take((size_t)nfirst * 4);             // first-pass digit counts / offsets of every mode
+    offs[4] = take((size_t)((nfirst + kScanBlock - 1) / kScanBlock + 1) * 4);  // their scan block sums
+    offs[5] = take((size_t)g * 256 * ntiles * 4);   // later-pass digit counts / offsets of a group
+    offs[6] = take((size_t)((g * 256 * ntiles + kScanBlock - 1) / kScanBlock + 1) * 4);  // their block sums
     offs[7] = take((size_t)2 * nchunk * c->Rp * 4); // partial vectors: a left and a right slot per chunk
-    offs[8] = take((size_t)((nfirst + kScanBlock - 1) / kScanBlock + 1) * 4);  // their scan block sums
     int64_t maxdim = 1;
     for (int k = 0; k < c->d; ++k) maxdim = c->dims[k] > maxdim ? c->dims[k] : maxdim;
-    offs[9] = take((size_t)maxdim * 4);             // start position of each row's run (one mode at a time)
-    offs[10] = take((size_t)((256 * ntiles + kScanBlock - 1) / kScanBlock + 1) * 4);  // later pass block sums
+    offs[8] = take((size_t)maxdim * 4);             // start position of each row's run (one mode at a time)
     if (o > c->det_scratch_bytes) {
         cudaFree(c->det_scratch);
         c->det_scratch = nullptr;
@@ -566,6 +652,11 @@ static gcp_status det_scratch(gcp_ctx *c, int64_t S, size_t *offs) {
             return e == cudaErrorMemoryAllocation ? GCP_ERR_OOM : GCP_ERR_CUDA;
         }
         c->det_scratch_bytes = o;
+        e = cudaMemsetAsync(c->det_scratch, 0, 4, c->st);
+        if (e != cudaSuccess) {
+            c->err = std::string("clearing deterministic MTTKRP scratch: ") + cudaGetErrorString(e);
+            return GCP_ERR_CUDA;
+        }
     }
     return GCP_OK;
 }
@@ -617,20 +708,20 @@ static cudaError_t allow_wide_scatter() {
 
 gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     const int64_t S = f0.s.p + f0.s.q;
-    size_t offs[11];
+    size_t offs[9];
     gcp_status s = det_scratch(c, S > 0 ? S : 1, offs);
     if (s) return s;
     char *base = static_cast<char *>(c->det_scratch);
     const int rw = rec_words(c->d);
-    int32_t *recs = reinterpret_cast<int32_t *>(base + offs[0]);
-    int32_t *histL = reinterpret_cast<int32_t *>(base + offs[1]);
-    int32_t *kA = reinterpret_cast<int32_t *>(base + offs[2]), *vA = reinterpret_cast<int32_t *>(base + offs[3]);
-    int32_t *kB = reinterpret_cast<int32_t *>(base + offs[4]), *vB = reinterpret_cast<int32_t *>(base + offs[5]);
-    int32_t *histF = reinterpret_cast<int32_t *>(base + offs[6]);
+    unsigned *ticket = reinterpret_cast<unsigned *>(base + offs[0]);
+    int32_t *recs = reinterpret_cast<int32_t *>(base + offs[1]);
+    int32_t *sortbuf = reinterpret_cast<int32_t *>(base + offs[2]);
+    int32_t *histF = reinterpret_cast<int32_t *>(base + offs[3]);
+    int32_t *bsumF = reinterpret_cast<int32_t *>(base + offs[4]);
+    int32_t *histL = reinterpret_cast<int32_t *>(base + offs[5]);
+    int32_t *bsumL = reinterpret_cast<int32_t *>(base + offs[6]);
     float *cvec = reinterpret_cast<float *>(base + offs[7]);
-    int32_t *bsumF = reinterpret_cast<int32_t *>(base + offs[8]);
-    int32_t *rowstart = reinterpret_cast<int32_t *>(base + offs[9]);
-    int32_t *bsumL = reinterpret_cast<int32_t *>(base + offs[10]);
+    int32_t *rowstart = reinterpret_cast<int32_t *>(base + offs[8]);
     cudaStream_t st = c->st;
     DET_CUDA(allow_wide_scatter());
 
@@ -646,7 +737,7 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
 
     // 2a. the first pass of every mode: counted and scanned once
     const int64_t ntiles = (S + kTile - 1) / kTile;
-    int bits[GCP_MAX_NDIM];
+    int bits[GCP_MAX_NDIM], npass[GCP_MAX_NDIM];
     FirstPlan FP{};
     FP.d = c->d;
     FP.rw = rw;
@@ -654,13 +745,18 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     for (int k = 0; k < c->d; ++k) {
         bits[k] = 1;
         while ((1ll << bits[k]) < c->dims[k]) ++bits[k];
-        FP.nb[k] = bits[k] > 8 && bits[k] <= 10 ? 1024 : 256;  // one 10-bit pass instead of 8 + 2
+        const bool wide = bits[k] > 8 && bits[k] <= 10;  // one 10-bit pass instead of 8 + 2
+        FP.nb[k] = wide ? 1024 : 256;
+        npass[k] = wide ? 1 : (bits[k] + 7) / 8;
         FP.soff[k] = k ? FP.soff[k - 1] + FP.nb[k - 1] : 0;
         FP.base[k] = nfirst;
         nfirst += (int64_t)FP.nb[k] * ntiles;
     }
-    k_radix_hist_first<<<(int)ntiles, kT, 0, st>>>(recs, S, FP, histF, (int)ntiles);
-    scan_two_part(histF, histF, nfirst, nullptr, bsumF, st);
+    const int used = FP.soff[c->d - 1] + FP.nb[c->d - 1];
+    const int G = used <= 3072 ? kHistTiles : 1;  // at most 48 KB of counters
+    k_radix_hist_first<<<(int)((ntiles + G - 1) / G), kT, (size_t)G * used * 4, st>>>(recs, S, FP, histF,
+                                                                                     (int)ntiles, G);
+    scan_two_part(histF, histF, nfirst, bsumF, ticket, st);
     DET_CUDA(cudaGetLastError());
 
     SegSpec P{};
@@ -673,55 +769,72 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     P.recs = recs;
     P.G = c->G;
     const int lanes = 1 << c->log2L;
-    for (int n = 0; n < c->d; ++n) {
-        P.n_mode = n;
-        P.rown = (int)c->rowoff[n];
-        // 2b. stable LSD radix sort of sample ids by row i_n
-        const bool wide = FP.nb[n] == 1024;
-        const int32_t *kin = recs + n;
-        int kstride = rw;
-        const int32_t *vin = nullptr;
-        int32_t *kout = kA, *vout = vA;
-        for (int shift = 0; shift < bits[n]; shift += wide ? 10 : 8) {
-            const int32_t *offsets = histF, *blks = bsumF;
-            int64_t obase = FP.base[n];
-            uint32_t sub = (uint32_t)((uint64_t)n * (uint64_t)S);
-            if (shift > 0) {  // a later pass: counted over the previous pass's order
-                k_radix_hist<256><<<(int)ntiles, kT, 0, st>>>(kin, kstride, S, shift, histL, (int)ntiles);
-                scan_two_part(histL, histL, 256 * ntiles, nullptr, bsumL, st);
-                offsets = histL;
-                blks = bsumL;
-                obase = 0;
-                sub = 0;
+    const int group = det_group(c, S);
+    // sort buffers of mode n (the j-th of its group): keys and ids, pass p
+    // writing pair p % 2
+    auto keys_of = [&](int j, int p) { return sortbuf + ((int64_t)j * 4 + 2 * (p & 1)) * S; };
+    auto ids_of = [&](int j, int p) { return sortbuf + ((int64_t)j * 4 + 2 * (p & 1) + 1) * S; };
+    for (int m0 = 0; m0 < c->d; m0 += group) {
+        const int m1 = m0 + group < c->d ? m0 + group : c->d;
+        // 2b. stable LSD radix sort of sample ids by row, the modes of the
+        // group side by side: pass p of every mode in one launch (the
+        // first passes by digit width)
+        for (int p = 0;; ++p) {
+            SortSegs segs[2] = {};  // 256-digit and 1024-digit passes
+            for (int n = m0; n < m1; ++n) {
+                if (p >= npass[n]) continue;
+                SortSegs &sg = segs[FP.nb[n] == 1024 ? 1 : 0];
+                SortSeg &q = sg.s[sg.nseg];
+                q.kin = p == 0 ? recs + n : keys_of(n - m0, p - 1);
+                q.kstride = p == 0 ? rw : 1;
+                q.vin = p == 0 ? nullptr : ids_of(n - m0, p - 1);
+                q.kout = keys_of(n - m0, p);
+                q.vout = ids_of(n - m0, p);
+                if (p == 0) {  // offsets from the shared first-pass scan
+                    q.obase = FP.base[n];
+                    q.sub = (uint32_t)((uint64_t)n * (uint64_t)S);
+                } else {       // offsets from this pass's own count
+                    q.obase = (int64_t)sg.nseg * 256 * ntiles;
+                    q.sub = (uint32_t)((uint64_t)sg.nseg * (uint64_t)S);
+                }
+                ++sg.nseg;
             }
-            if (wide)
-                k_radix_scatter<1024><<<(int)ntiles, kT, scatter_smem_bytes<1024>(), st>>>(
-                    kin, kstride, vin, S, shift, offsets, blks, obase, sub, (int)ntiles, kout, vout);
-            else
-                k_radix_scatter<256><<<(int)ntiles, kT, scatter_smem_bytes<256>(), st>>>(
-                    kin, kstride, vin, S, shift, offsets, blks, obase, sub, (int)ntiles, kout, vout);
+            if (segs[0].nseg + segs[1].nseg == 0) break;
+            const int shift = 8 * p;
+            if (p > 0) {  // later passes: counted over the previous pass's order
+                const int per = (int)((ntiles + kHistTiles - 1) / kHistTiles);
+                k_radix_hist<256><<<segs[0].nseg * per, kT, 0, st>>>(segs[0], S, shift, histL, (int)ntiles);
+                scan_two_part(histL, histL, (int64_t)segs[0].nseg * 256 * ntiles, bsumL, ticket, st);
+            }
+            const int32_t *offsets = p == 0 ? histF : histL, *blks = p == 0 ? bsumF : bsumL;
+            if (segs[0].nseg)
+                k_radix_scatter<256><<<(int)(segs[0].nseg * ntiles), kT, scatter_smem_bytes<256>(), st>>>(
+                    segs[0], S, shift, offsets, blks, (int)ntiles);
+            if (segs[1].nseg)
+                k_radix_scatter<1024><<<(int)(segs[1].nseg * ntiles), kT, scatter_smem_bytes<1024>(), st>>>(
+                    segs[1], S, shift, offsets, blks, (int)ntiles);
             DET_CUDA(cudaGetLastError());
-            kin = kout;
-            vin = vout;
-            kstride = 1;
-            kout = (kout == kA) ? kB : kA;
-            vout = (vout == vA) ? vB : vA;
         }
-        // 3. chunked segmented reduction over the sorted samples
-        const int64_t nch = (S + kChunk - 1) / kChunk;
-        const int grid = grid_for(nch * lanes, kT);
-        if (c->Abf)
-            launch_seg_samples<__nv_bfloat16>(P, c->cols, grid, kin, vin, S, cvec, rowstart, st);
-        else
-            launch_seg_samples<float>(P, c->cols, grid, kin, vin, S, cvec, rowstart, st);
-        DET_CUDA(cudaGetLastError());
-        // 4. the runs that cross chunk edges: a lane per chunk decides, a warp sums
-        const int fgrid = grid_for(((nch + 31) / 32) * 32, kT);  // a lane per chunk
-        if (c->cols == 8)
-            k_seg_finish<8><<<fgrid, kT, 0, st>>>(P, kin, S, cvec, rowstart);
-        else
-            k_seg_finish<4><<<fgrid, kT, 0, st>>>(P, kin, S, cvec, rowstart);
-        DET_CUDA(cudaGetLastError());
+        for (int n = m0; n < m1; ++n) {
+            P.n_mode = n;
+            P.rown = (int)c->rowoff[n];
+            const int32_t *kin = keys_of(n - m0, npass[n] - 1), *vin = ids_of(n - m0, npass[n] - 1);
+            // 3. chunked segmented reduction over the sorted samples
+            const int64_t nch = (S + kChunk - 1) / kChunk;
+            const int grid = grid_for(nch * lanes, kT);
+            if (c->Abf)
+                launch_seg_samples<__nv_bfloat16>(P, c->cols, grid, kin, vin, S, cvec, rowstart, st);
+            else
+                launch_seg_samples<float>(P, c->cols, grid, kin, vin, S, cvec, rowstart, st);
+            DET_CUDA(cudaGetLastError());
+            // 4. the runs that cross chunk edges: a lane per chunk decides, a warp sums
+            const int fgrid = grid_for(((nch + 31) / 32) * 32, kT);  // a lane per chunk
+            if (c->cols == 8)
+                k_seg_finish<8><<<fgrid, kT, 0, st>>>(P, kin, S, cvec, rowstart);
+            else
+                k_seg_finish<4><<<fgrid, kT, 0, st>>>(P, kin, S, cvec, rowstart);
+            DET_CUDA(cudaGetLastError());
+        }
     }
     return GCP_OK;
 }

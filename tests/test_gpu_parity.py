@@ -526,6 +526,30 @@ def test_deterministic_mttkrp_semi_stratified_scaled_and_missing_samples(env):
     full.close()
 
 
+def test_deterministic_mttkrp_modes_sorted_in_two_groups(env):
+    """An 8-way tensor with 8.4e6 samples: the sort buffers of all eight
+    modes (16 B per sample and mode) pass 1 GiB, so the modes are sorted in
+    a group of seven side by side and then one alone, with one-pass and
+    two-pass modes and both digit widths in the group.  Bit-stable, and equal to
+    the oracle."""
+    gcp, torch = env
+    dims, R = [2000, 600, 56, 52, 48, 44, 40, 36], 4  # 11-bit rows: two passes; 10-bit: one wide pass
+    coords, vals, factors = problem(dims, 3000, R, "gaussian", 881)
+    p = q = (1 << 22) + 5000
+    assert 16 * (p + q) * 8 > 1 << 30 and 16 * (p + q) * 7 <= 1 << 30
+    det = gcp.gcp_create(dims, coords, vals, R, "gaussian", seed=31, mttkrp="deterministic")
+    det.set_factors(factors)
+    L1, G1 = gpu_grad(gcp, torch, det, 2, p, q)
+    L2, G2 = gpu_grad(gcp, torch, det, 2, p, q)
+    assert L1 == L2 and np.array_equal(G1.view(np.uint32), G2.view(np.uint32))
+    idx, x, wt, _ = oracle.stratified_samples(31, 2, p, q, dims, coords, vals)
+    Lo, Go = oracle.sampled_loss_grad(dims, factors, "gaussian", idx, x, wt)
+    assert abs(L1 - Lo) <= TOL_FP32 * abs(Lo)
+    for n, (a, b) in enumerate(zip(split(G1, dims, R), Go)):
+        assert rel_err(a, b) <= TOL_FP32, (n, rel_err(a, b))
+    det.close()
+
+
 @pytest.fixture(scope="module")
 def bernoulli_full():
     def make():

@@ -51,3 +51,34 @@ def test_single_rank_needs_no_process_group():
 
     value, slowest = bench.combine_ranks(0.5, 100, 1, None)
     assert value == pytest.approx(200.0) and slowest == 0.5
+
+
+def test_clock_record_summaries():
+    """The bench's clock records: NVML clock-event reason bits decode to the
+    names the timing rules use, and nvidia-smi lines parse the same way; with
+    neither available the record is empty, not an error."""
+    import bench
+
+    nv = bench.NvmlClocks(0)
+    nv.samples = [(2070.0, 0x0), (2070.0, 0x4), (1995.0, 0x4 | 0x40), (2070.0, 0x1)]
+    nv.max_mhz = 2070.0
+    s = nv.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 4
+    assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]  # 0x1 (idle) is not a slowdown
+    smi = bench.ClockSampler(0)
+    smi.lines = ["0, 2070, 2070, 900.5, 0x4, Not Active, Not Active, Not Active, Active",
+                 "0, 1800, 2070, 1400.0, 0x8, Active, Not Active, Not Active, Not Active"]
+    s = smi.summary()
+    assert s["sm_mhz"] == 1935.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    if not torch_cuda_available():
+        rec = bench.ClockRecord(0)
+        with rec:
+            pass
+        assert rec.summary()["samples"] == 0
+
+
+def torch_cuda_available():
+    import torch
+
+    return torch.cuda.is_available()
