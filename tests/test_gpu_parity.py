@@ -313,17 +313,22 @@ def test_fit_reduces_objective(env):
 
 
 # ----------------------------------------------------------- edge cases
-def test_empty_sample_sets(env):
+@pytest.mark.parametrize("mttkrp", ["atomic", "deterministic", "nonfused"])
+def test_empty_sample_sets(env, mttkrp):
     gcp, torch = env
     w = synth.workload_small_gaussian()
-    ctx = gcp.gcp_create(w["dims"], w["coords"], w["vals"], 4, "gaussian", seed=1)
+    ctx = gcp.gcp_create(w["dims"], w["coords"], w["vals"], 4, "gaussian", seed=1, mttkrp=mttkrp)
     ctx.set_factors(w["factors"])
     L, G = gpu_grad(gcp, torch, ctx, 0, 0, 0)
     assert L == 0.0 and not np.any(G)
-    L, G = gpu_grad(gcp, torch, ctx, 0, 37, 0)  # nonzeros only
+    L, G = gpu_grad(gcp, torch, ctx, 0, 37, 0)  # nonzeros only: one ragged tile
     idx, x, wt, _ = oracle.stratified_samples(1, 0, 37, 0, w["dims"], w["coords"], w["vals"])
     Lo, Go = oracle.sampled_loss_grad(w["dims"], w["factors"], "gaussian", idx, x, wt)
     assert abs(L - Lo) <= TOL_FP32 * abs(Lo)
+    for n, (a, b) in enumerate(zip(split(G, w["dims"], 4), Go)):
+        assert rel_err(a, b) <= TOL_FP32, (n, rel_err(a, b))
+    L, G = gpu_grad(gcp, torch, ctx, 0, 0, 0)  # and empty again after a non-empty call
+    assert L == 0.0 and not np.any(G)
     ctx.close()
 
 
@@ -669,24 +674,26 @@ def step_gradient(gcp, ctx, factors, it, p, q, g_max):
     return recover_gradient(flat(factors), flat(ctx.get_factors()), prm)
 
 
-@pytest.mark.parametrize("dtype", ["fp32", "bf16"])
-def test_step_folded_gradient_matches_oracle(env, dtype):
+@pytest.mark.parametrize("dtype,mttkrp", [("fp32", "atomic"), ("bf16", "atomic"), ("fp32", "deterministic"),
+                                          ("fp32", "nonfused")])
+def test_step_folded_gradient_matches_oracle(env, dtype, mttkrp):
     """The gradient inside gcp_step (fused pass, then the epilogue's replica
-    fold) element by element against the oracle's sampled gradient (Eq.
+    fold; for the deterministic and non-fused variants their own gradient,
+    then Adam) element by element against the oracle's sampled gradient (Eq.
     gcp-gradient), per mode, at 1e-5.  The Zipf tensor's 200-row mode is
     fully replicated, its other modes have replicated head rows carried in
     the nonzero records, and drawn zero cells reach unreplicated rows."""
     gcp, torch = env
     w = synth.workload_zipf_count(scale=0.01)
     dims, p, q, R = w["dims"], 9000, 9001, 32
-    ctx = gcp.gcp_create(dims, w["coords"], w["vals"], R, "poisson", dtype=dtype, seed=53)
+    ctx = gcp.gcp_create(dims, w["coords"], w["vals"], R, "poisson", dtype=dtype, seed=53, mttkrp=mttkrp)
     fac = [bf16_round(x) for x in w["factors"]] if dtype == "bf16" else w["factors"]
     idx, x, wt, _ = oracle.stratified_samples(53, 2, p, q, dims, w["coords"], w["vals"])
     _, Go = oracle.sampled_loss_grad(dims, fac, "poisson", idx, x, wt)
     g_max = max(np.abs(g).max() for g in Go)
     G = step_gradient(gcp, ctx, w["factors"], 2, p, q, g_max)
     for n, (a, b) in enumerate(zip(split(G, dims, R), Go)):
-        assert rel_err(a, b) <= TOL_FP32, (dtype, n, rel_err(a, b))
+        assert rel_err(a, b) <= TOL_FP32, (dtype, mttkrp, n, rel_err(a, b))
     ctx.close()
 
 
