@@ -952,10 +952,48 @@ def run_ours(args):
     ms = slowest_s * 1e3
     ms_per_step = ms / args.steps
 
-    # end to end through the public API with host buffers: factors in from
-    # pinned host memory, gradient and loss back to the host every step
+    # end to end through the public API with host buffers, the same step as
+    # `value` (gcp_step): every step the factors come in from pinned host
+    # memory and the host reads the step's loss (8 B back).  The host reads
+    # step i's loss after it has issued step i + 1, as a training loop that
+    # logs its losses does, so the GPU does not wait on the host between steps
     n_e2e = max(3, min(args.steps, 200))
     A_host = torch.from_numpy(np.concatenate([a.ravel() for a in w["factors"]])).pin_memory()
+    dl = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in range(2)]
+    dl_host = [torch.zeros(1, dtype=torch.float64).pin_memory() for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
+
+    def e2e_issue(i):
+        assert gcp.load().gcp_set_factors(ctx.handle, A_host.data_ptr()) == 0
+        ctx.step(i, p, q, adam, i + 1, dloss=dl[i % 2])
+        dl_host[i % 2].copy_(dl[i % 2], non_blocking=True)
+        done[i % 2].record(stream)
+
+    def e2e_read(i):
+        done[i % 2].synchronize()
+        return dl_host[i % 2].item()
+
+    def e2e_loop(first, n):
+        losses = []
+        for i in range(first, first + n):
+            e2e_issue(i)
+            if i > first:
+                losses.append(e2e_read(i - 1))
+        losses.append(e2e_read(first + n - 1))
+        return losses
+
+    e2e_loop(20_000, 3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_losses = e2e_loop(0, n_e2e)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    assert len(e2e_losses) == n_e2e and all(math.isfinite(v) for v in e2e_losses)
+    e2e_value, _ = combine_ranks(e2e_s, S * n_e2e, world, dist, device="cuda")
+    # the same with the whole gradient out instead (gcp_grad to pinned host
+    # memory, then gcp_adam_step): the gradient API's round trip
     G_host = torch.empty(ctx.num_params, dtype=torch.float32).pin_memory()
     for i in range(3):
         ctx.set_factors(A_host.numpy())
@@ -965,13 +1003,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(n_e2e):
-        _check = gcp.load().gcp_set_factors(ctx.handle, A_host.data_ptr())
-        assert _check == 0
-        loss, _ = ctx.grad(i, p, q, G_out=G_host)
+        assert gcp.load().gcp_set_factors(ctx.handle, A_host.data_ptr()) == 0
+        ctx.grad(i, p, q, G_out=G_host)
         ctx.adam_step(adam, i + 1)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value, _ = combine_ranks(e2e_s, S * n_e2e, world, dist, device="cuda")
+    e2e_g_value, _ = combine_ranks(time.perf_counter() - t0, S * n_e2e, world, dist, device="cuda")
     ctx.close()
 
     # BF16 factor storage, same workload
@@ -1038,7 +1074,14 @@ def run_ours(args):
                      "parallelism": f"replicas{world}"},
             "roofline": roofline, "cpu_baseline": base,
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(A_host.numel() * 4),
-                    "d2h_bytes_per_step": int(G_host.numel() * 4 + 8)},
+                    "d2h_bytes_per_step": 8,
+                    "what": "gcp_step per step with the factors copied in from pinned host memory and the "
+                            "loss read back by the host (step i's loss read once step i + 1 is issued)",
+                    "gradient_out": {"value": e2e_g_value, "unit": "samples/s",
+                                     "h2d_bytes_per_step": int(A_host.numel() * 4),
+                                     "d2h_bytes_per_step": int(G_host.numel() * 4 + 8),
+                                     "what": "gcp_grad with the gradient and loss copied to pinned host "
+                                             "memory, then gcp_adam_step"}},
             # per step (gcp_step): k_fused and the k_post_step epilogue
             "gpu_launches": 2 * args.steps, "clocks": clocks,
             "variants": {"bf16_factors": {"value": bf16_value, "unit": "samples/s",
