@@ -11,7 +11,10 @@
 //      lookup of a sample reads one 16-byte vector (d <= 3);
 //   2. per mode n, a stable LSD radix sort (8-bit digits, or one 10-bit
 //      pass) orders the sample ids by row i_n, ties in sample order.  The
-//      first pass of every mode is counted and scanned once for all modes;
+//      first pass of every mode is counted and scanned once for all modes,
+//      and the modes are sorted side by side: pass p of every mode that has
+//      one is a single launch over all their tiles, so that it fills whole
+//      waves of resident blocks;
 //   3. a chunked segmented reduction walks the sorted list in chunks of kChunk
 //      (64) positions, one chunk per group of lanes, recomputing the Khatri-Rao row
 //      products.  A run of equal rows that lies inside one chunk is stored to
