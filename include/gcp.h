@@ -77,10 +77,11 @@ typedef enum { GCP_FP32 = 0, GCP_BF16 = 1 } gcp_factor_dtype;
 typedef enum {
     GCP_MTTKRP_ATOMIC = 0,       /* fused scatter with FP32 vector atomics (Sec. 3.1.2) */
     GCP_MTTKRP_DETERMINISTIC = 1, /* sort by row + segmented sums, bit-stable run to run;
-                                     grows a scratch buffer on first use of a sample count
-                                     (S = p + q): about S x (16 B per record + 16 B per mode
-                                     sorted side by side, those capped at 1 GiB) + 32 B per
-                                     64 samples x rank; GCP_ERR_OOM if it cannot */
+                                     grows a scratch buffer for the largest sample count
+                                     S = p + q seen: a 16, 32 or 64 B record per sample, 16 B
+                                     per sample and mode for the modes sorted side by side
+                                     (at most 1 GiB of those), 8 x padded rank B per 64
+                                     samples, and small counts; GCP_ERR_OOM if it cannot */
     GCP_MTTKRP_NONFUSED = 2       /* sampling writes the gradient tensor, then a separate
                                      atomic MTTKRP reads it (the unfused form of Sec. 3.1.2) */
 } gcp_mttkrp_t;
