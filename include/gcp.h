@@ -80,8 +80,9 @@ typedef enum {
                                      grows a scratch buffer for the largest sample count
                                      S = p + q seen: a 16, 32 or 64 B record per sample, 16 B
                                      per sample and mode for the modes sorted side by side
-                                     (at most 1 GiB of those), 8 x padded rank B per 64
-                                     samples, and small counts; GCP_ERR_OOM if it cannot */
+                                     (as many as fit 1 GiB, at least one), 8 x padded rank B
+                                     per 64 samples, and small counts; GCP_ERR_OOM if it
+                                     cannot */
     GCP_MTTKRP_NONFUSED = 2       /* sampling writes the gradient tensor, then a separate
                                      atomic MTTKRP reads it (the unfused form of Sec. 3.1.2) */
 } gcp_mttkrp_t;
