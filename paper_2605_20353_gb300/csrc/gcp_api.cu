@@ -100,6 +100,9 @@ void destroy_buffers(gcp_ctx *c) {
     cudaFree(c->dloss);
     cudaFree(c->status);
     cudaFree(c->det_scratch);
+    if (c->det_side) cudaStreamDestroy(c->det_side);
+    if (c->det_fork) cudaEventDestroy(c->det_fork);
+    if (c->det_join) cudaEventDestroy(c->det_join);
     cudaFree(c->nf_coord);
     cudaFree(c->nf_val);
     cudaFree(c->hot_slot);

@@ -146,6 +146,8 @@ struct gcp_ctx {
     // deterministic MTTKRP scratch
     void *det_scratch = nullptr;
     size_t det_scratch_bytes = 0;
+    cudaStream_t det_side = nullptr;             // second stream of the sort (its wide passes)
+    cudaEvent_t det_fork = nullptr, det_join = nullptr;
 
     // non-fused MTTKRP: the materialised gradient tensor
     int32_t *nf_coord = nullptr;

@@ -777,6 +777,7 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
     // writing pair p % 2
     auto keys_of = [&](int j, int p) { return sortbuf + ((int64_t)j * 4 + 2 * (p & 1)) * S; };
     auto ids_of = [&](int j, int p) { return sortbuf + ((int64_t)j * 4 + 2 * (p & 1) + 1) * S; };
+    bool joined = true;  // no side-stream work outstanding
     for (int m0 = 0; m0 < c->d; m0 += group) {
         const int m1 = m0 + group < c->d ? m0 + group : c->d;
         // 2b. stable LSD radix sort of sample ids by row, the modes of the
@@ -810,13 +811,36 @@ gcp_status gcpk_det_grad(gcp_ctx *c, const gcpk::FusedSpec &f0, int *blocks) {
                 scan_two_part(histL, histL, (int64_t)segs[0].nseg * 256 * ntiles, bsumL, ticket, st);
             }
             const int32_t *offsets = p == 0 ? histF : histL, *blks = p == 0 ? bsumF : bsumL;
+            // both widths in one pass: the 1024-digit launch runs on the side
+            // stream beside the 256-digit one, so that each fills the other's
+            // partial waves (both read only the records and the first-pass
+            // offsets, and write their own modes' buffers)
+            cudaStream_t wst = st;
+            if (segs[0].nseg && segs[1].nseg) {
+                if (!c->det_side) {
+                    DET_CUDA(cudaStreamCreateWithFlags(&c->det_side, cudaStreamNonBlocking));
+                    DET_CUDA(cudaEventCreateWithFlags(&c->det_fork, cudaEventDisableTiming));
+                    DET_CUDA(cudaEventCreateWithFlags(&c->det_join, cudaEventDisableTiming));
+                }
+                DET_CUDA(cudaEventRecord(c->det_fork, st));
+                DET_CUDA(cudaStreamWaitEvent(c->det_side, c->det_fork, 0));
+                wst = c->det_side;
+            }
+            if (segs[1].nseg)
+                k_radix_scatter<1024><<<(int)(segs[1].nseg * ntiles), kT, scatter_smem_bytes<1024>(), wst>>>(
+                    segs[1], S, shift, offsets, blks, (int)ntiles);
             if (segs[0].nseg)
                 k_radix_scatter<256><<<(int)(segs[0].nseg * ntiles), kT, scatter_smem_bytes<256>(), st>>>(
                     segs[0], S, shift, offsets, blks, (int)ntiles);
-            if (segs[1].nseg)
-                k_radix_scatter<1024><<<(int)(segs[1].nseg * ntiles), kT, scatter_smem_bytes<1024>(), st>>>(
-                    segs[1], S, shift, offsets, blks, (int)ntiles);
             DET_CUDA(cudaGetLastError());
+            if (wst != st) {
+                DET_CUDA(cudaEventRecord(c->det_join, wst));
+                joined = false;
+            }
+        }
+        if (!joined) {  // the wide modes' sort is done before their reduction
+            DET_CUDA(cudaStreamWaitEvent(st, c->det_join, 0));
+            joined = true;
         }
         for (int n = m0; n < m1; ++n) {
             P.n_mode = n;
