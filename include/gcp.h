@@ -82,7 +82,9 @@ typedef enum {
                                      per sample and mode for the modes sorted side by side
                                      (as many as fit 1 GiB, at least one), 8 x padded rank B
                                      per 64 samples, and small counts; GCP_ERR_OOM if it
-                                     cannot */
+                                     cannot.  It also creates a second stream for its sort
+                                     on first use, so make the first call with the largest
+                                     sample count outside stream capture */
     GCP_MTTKRP_NONFUSED = 2       /* sampling writes the gradient tensor, then a separate
                                      atomic MTTKRP reads it (the unfused form of Sec. 3.1.2) */
 } gcp_mttkrp_t;
