@@ -471,10 +471,21 @@ __global__ void k_sumsq_finish(const double *__restrict__ partial, int nblocks, 
     if (!isfinite(t)) atomicOr(status, 1 << GCP_ERR_NONFINITE);
 }
 
+// Copy `rows` rows of `width` bytes between arrays whose rows are dpitch
+// and spitch bytes apart.  With equal pitches and no padding the rows are
+// one contiguous block and go as one plain copy (the strided form moves
+// each row separately).
+static cudaError_t copy_rows(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width, size_t rows,
+                      cudaStream_t st) {
+    if (dpitch == width && spitch == width)
+        return cudaMemcpyAsync(dst, src, width * rows, cudaMemcpyDefault, st);
+    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyDefault, st);
+}
+
 gcp_status copy_grad_out(gcp_ctx *c, float *G_out) {
     if (!G_out) return GCP_OK;
-    GCP_CUDA(c, cudaMemcpy2DAsync(G_out, (size_t)c->R * 4, c->G, (size_t)c->Rp * 4, (size_t)c->R * 4,
-                                  (size_t)c->total_rows, cudaMemcpyDefault, c->st));
+    GCP_CUDA(c, copy_rows(G_out, (size_t)c->R * 4, c->G, (size_t)c->Rp * 4, (size_t)c->R * 4,
+                                  (size_t)c->total_rows, c->st));
     return GCP_OK;
 }
 
@@ -707,8 +718,8 @@ int64_t gcp_num_params(const gcp_ctx *c) { return c ? c->total_rows * c->R : 0; 
 gcp_status gcp_set_factors(gcp_ctx *c, const float *A) {
     if (!c || !A) return fail(c, GCP_ERR_ARG, "NULL argument");
     DeviceGuard g(c->device);
-    GCP_CUDA(c, cudaMemcpy2DAsync(c->A, (size_t)c->Rp * 4, A, (size_t)c->R * 4, (size_t)c->R * 4,
-                                  (size_t)c->total_rows, cudaMemcpyDefault, c->st));
+    GCP_CUDA(c, copy_rows(c->A, (size_t)c->Rp * 4, A, (size_t)c->R * 4, (size_t)c->R * 4,
+                                  (size_t)c->total_rows, c->st));
     return refresh_bf16(c);
 }
 
@@ -716,8 +727,8 @@ gcp_status gcp_set_factor(gcp_ctx *c, int32_t mode, const float *A_mode) {
     if (!c || !A_mode) return fail(c, GCP_ERR_ARG, "NULL argument");
     if (mode < 0 || mode >= c->d) return fail(c, GCP_ERR_ARG, "mode out of range");
     DeviceGuard g(c->device);
-    GCP_CUDA(c, cudaMemcpy2DAsync(c->A + c->rowoff[mode] * c->Rp, (size_t)c->Rp * 4, A_mode, (size_t)c->R * 4,
-                                  (size_t)c->R * 4, (size_t)c->dims[mode], cudaMemcpyDefault, c->st));
+    GCP_CUDA(c, copy_rows(c->A + c->rowoff[mode] * c->Rp, (size_t)c->Rp * 4, A_mode, (size_t)c->R * 4,
+                                  (size_t)c->R * 4, (size_t)c->dims[mode], c->st));
     return refresh_bf16(c);
 }
 
@@ -727,16 +738,16 @@ gcp_status gcp_set_factor_list(gcp_ctx *c, const float *const *A_modes) {
         if (!A_modes[k]) return fail(c, GCP_ERR_ARG, "NULL factor pointer");
     DeviceGuard g(c->device);
     for (int k = 0; k < c->d; ++k)
-        GCP_CUDA(c, cudaMemcpy2DAsync(c->A + c->rowoff[k] * c->Rp, (size_t)c->Rp * 4, A_modes[k], (size_t)c->R * 4,
-                                      (size_t)c->R * 4, (size_t)c->dims[k], cudaMemcpyDefault, c->st));
+        GCP_CUDA(c, copy_rows(c->A + c->rowoff[k] * c->Rp, (size_t)c->Rp * 4, A_modes[k], (size_t)c->R * 4,
+                                      (size_t)c->R * 4, (size_t)c->dims[k], c->st));
     return refresh_bf16(c);
 }
 
 gcp_status gcp_get_factors(gcp_ctx *c, float *A_out) {
     if (!c || !A_out) return fail(c, GCP_ERR_ARG, "NULL argument");
     DeviceGuard g(c->device);
-    GCP_CUDA(c, cudaMemcpy2DAsync(A_out, (size_t)c->R * 4, c->A, (size_t)c->Rp * 4, (size_t)c->R * 4,
-                                  (size_t)c->total_rows, cudaMemcpyDefault, c->st));
+    GCP_CUDA(c, copy_rows(A_out, (size_t)c->R * 4, c->A, (size_t)c->Rp * 4, (size_t)c->R * 4,
+                                  (size_t)c->total_rows, c->st));
     return collect(c);
 }
 
